@@ -1,0 +1,239 @@
+/*
+ * ktune.h - C ABI of the GB300 counter-guided tuning-space search step.
+ *
+ * Method: J. Filipovic et al., "Using hardware performance counters to speed
+ * up autotuning convergence on GPUs", arXiv 2102.05297.  One search step
+ * (Section 3.2's workflow, Algorithm 1's outer loop) decodes and filters every
+ * configuration of a tuning space (Section 1), predicts its counter vector
+ * with a per-problem model (Section 3.3), scores it against the bottlenecks of
+ * the last profiled configuration (Sections 3.4-3.5, Eqs. global-read ...
+ * paral, fp32_reaction, score, score_normalization) and selects the next
+ * configurations (Section 3.6, Algorithm 1).
+ *
+ * Conventions
+ *  - Every call returns int: KTUNE_OK (0) or a negative KTUNE_E* code.  On an
+ *    error, ktune_last_error() returns a message for the calling thread.
+ *    No C++ exception crosses this boundary.
+ *  - The library owns every handle it creates; release each with its
+ *    *_destroy call.  The caller owns every buffer it passes in.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls taking host buffers synchronise that stream before they
+ *    return; *_device calls only enqueue work.
+ *  - A configuration is identified by its raw index: its mixed-radix number
+ *    over the parameters' value indices ("digits"), LAST parameter varying
+ *    fastest.  TS (Algorithm 1's array of configurations) lists the valid
+ *    configurations in ascending raw order; a configuration's position in TS
+ *    is its ordinal.
+ *  - Handles are not thread-safe; use one handle from one thread at a time.
+ */
+#ifndef KTUNE_H
+#define KTUNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KTUNE_OK 0
+#define KTUNE_EINVAL (-1)     /* invalid argument or descriptor */
+#define KTUNE_ENOMEM (-2)     /* device or host allocation failed */
+#define KTUNE_EMODEL (-3)     /* model blob malformed or inconsistent with the space */
+#define KTUNE_EXHAUSTED (-4)  /* fewer unevaluated configurations than requested */
+#define KTUNE_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define KTUNE_ECUDA (-6)      /* a CUDA runtime call failed */
+#define KTUNE_ESTATE (-7)     /* call not valid in the handle's current state */
+
+#define KTUNE_MAX_PARAMS 16
+#define KTUNE_MAX_VALUES 16
+#define KTUNE_MAX_COUNTERS 64
+#define KTUNE_MAX_DEPTH 14
+#define KTUNE_MAX_K 64
+
+/* space flags */
+#define KTUNE_MATERIALISE 0   /* TS stored on the device, 8 bytes per valid configuration */
+#define KTUNE_ON_THE_FLY 1    /* nothing stored; every step re-decodes all raw indices */
+
+/* search select modes (Section 3.6) */
+#define KTUNE_SELECT_SAMPLE 0 /* weighted draws without replacement (Algorithm 1) */
+#define KTUNE_SELECT_TOPK 1   /* the k highest scores, ties to the lower raw index */
+
+/* Constraint bytecode opcodes: a stack program over int64 parameter values.
+ * Each REQUIRE pops one value; a configuration is valid iff every popped value
+ * is non-zero.  VAL j pushes parameter j's value, CONST c pushes the int32 c,
+ * CONST64 lo hi pushes (hi << 32) | (uint32)lo.  Binary operators pop b then a
+ * and push a OP b; DIV and MOD truncate toward zero and give 0 for a zero
+ * divisor; comparisons and logic ops push 0 or 1; arithmetic wraps mod 2^64. */
+enum {
+  KTUNE_OP_VAL = 1, KTUNE_OP_CONST = 2, KTUNE_OP_ADD = 3, KTUNE_OP_SUB = 4,
+  KTUNE_OP_MUL = 5, KTUNE_OP_DIV = 6, KTUNE_OP_MOD = 7, KTUNE_OP_EQ = 8,
+  KTUNE_OP_NE = 9, KTUNE_OP_LT = 10, KTUNE_OP_LE = 11, KTUNE_OP_GT = 12,
+  KTUNE_OP_GE = 13, KTUNE_OP_AND = 14, KTUNE_OP_OR = 15, KTUNE_OP_NOT = 16,
+  KTUNE_OP_REQUIRE = 17, KTUNE_OP_CONST64 = 18
+};
+
+/* Counter roles: Table "tab:pcs" in table order, then the thread-count
+ * pseudo-counter of Section 3.4.2 and an inert role (predicted, never reacted
+ * to). */
+enum {
+  KTUNE_PC_DRAM_RT = 0, KTUNE_PC_DRAM_WT, KTUNE_PC_L2_RT, KTUNE_PC_L2_WT,
+  KTUNE_PC_TEX_RWT, KTUNE_PC_LOC_O, KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT,
+  KTUNE_PC_INST_F32, KTUNE_PC_INST_F64, KTUNE_PC_INST_INT, KTUNE_PC_INST_MISC,
+  KTUNE_PC_INST_LDST, KTUNE_PC_INST_CONT, KTUNE_PC_INST_BCONV,
+  KTUNE_PC_INST_EXE, KTUNE_PC_INST_ISSUE_U, KTUNE_PC_DRAM_U, KTUNE_PC_L2_U,
+  KTUNE_PC_TEX_U, KTUNE_PC_SHR_U, KTUNE_PC_SM_E, KTUNE_PC_WARP_E,
+  KTUNE_PC_WARP_NP_E, KTUNE_PC_GLOBAL, KTUNE_PC_INERT, KTUNE_PC_N_ROLES
+};
+
+typedef struct ktune_space ktune_space;
+typedef struct ktune_model ktune_model;
+typedef struct ktune_search ktune_search;
+
+/* Tuning space (Section 1: the cross product of the parameters' value sets
+ * pruned by constraints).
+ *   n_params   1..KTUNE_MAX_PARAMS
+ *   n_values   [n_params], each 1..KTUNE_MAX_VALUES
+ *   values     the n_params value lists concatenated, each strictly ascending
+ *   bytecode   [n_bytecode] constraint program (may be empty)
+ * Limits: the raw size (product of n_values) is below 2^40; each constraint
+ * group (a bytecode span that starts and ends with an empty stack) depends on
+ * parameters whose value combinations number at most 2^20. */
+typedef struct {
+  int n_params;
+  const int *n_values;
+  const int64_t *values;
+  const int32_t *bytecode;
+  int n_bytecode;
+} ktune_space_desc;
+
+/* Search options.  k: configurations per step (Algorithm 1's n, 1..64);
+ * inst_reaction: Section 3.4.2 threshold (0.7 default, 0.5 for instruction-
+ * bound problems); gamma: the normalisation cut-off (-0.25); cores: CUDA cores
+ * for Eq. paral; seed / search_id: Philox4x32-10 key and counter word;
+ * select: KTUNE_SELECT_*. */
+typedef struct {
+  int k;
+  double inst_reaction;
+  float gamma;
+  double cores;
+  uint64_t seed;
+  uint32_t search_id;
+  int select;
+} ktune_search_opts;
+
+/* Version of the C ABI (major * 100 + minor). */
+int ktune_abi_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ktune_last_error(void);
+
+/* ---- space (Section 1; Algorithm 1 input TS) ------------------------------
+ * Validates the descriptor (KTUNE_EINVAL), then enumerates the space on the
+ * device: every raw index is decoded into digits and filtered by the
+ * constraints.  With KTUNE_MATERIALISE the valid configurations are stored in
+ * ascending raw order as one uint64 per configuration (digit j in bits
+ * 4j..4j+3); with KTUNE_ON_THE_FLY only per-tile valid counts are kept and
+ * every step re-decodes.  Enqueued on `stream` and synchronised before return. */
+int ktune_space_create(const ktune_space_desc *desc, int flags, void *stream,
+                       ktune_space **out);
+int ktune_space_destroy(ktune_space *space);
+/* Number of valid and raw configurations. */
+int ktune_space_count(const ktune_space *space, int64_t *n_valid, int64_t *n_raw);
+/* Parameter values of the configuration with raw index `raw` (host, n_params
+ * int64 written to values_out).  KTUNE_EINVAL if raw is out of range; the
+ * configuration need not be valid. */
+int ktune_space_decode(const ktune_space *space, int64_t raw, int64_t *values_out);
+/* Raw indices of TS[first .. first+count) copied to the host buffer out_raw
+ * (materialised spaces only; KTUNE_ESTATE otherwise). */
+int ktune_space_valid_raw(const ktune_space *space, int64_t first, int64_t count,
+                          int64_t *out_raw);
+/* Digits of TS[first .. first+count) written to the HOST buffer out as
+ * uint8 [count][n_params] (materialised spaces only; KTUNE_ESTATE otherwise). */
+int ktune_space_valid_digits(const ktune_space *space, int64_t first, int64_t count,
+                             uint8_t *out);
+/* Device pointer to TS's packed digits (materialised spaces; NULL otherwise).
+ * Owned by the space; valid until ktune_space_destroy. */
+const uint64_t *ktune_space_packed_device(const ktune_space *space);
+
+/* ---- model (Section 3.3) ----------------------------------------------------
+ * Parses a model blob (little-endian):
+ *   uint32 magic 0x314D544B ("KTM1"), uint32 version 1, uint32 kind (1 = tree
+ *   ensemble), uint32 K (1..KTUNE_MAX_COUNTERS), int32 roles[K];
+ *   kind 1: then per counter: uint32 n_nodes, int32 feature[n] (-1 = leaf),
+ *   int32 threshold[n] (right iff digit > threshold), int32 left[n],
+ *   int32 right[n], float value[n] (leaf values, finite); node 0 is the root.
+ * Checks every index against the space (KTUNE_EMODEL), pads the trees to
+ * complete trees of the ensemble's depth (<= KTUNE_MAX_DEPTH) and copies them
+ * to the device.  The model keeps a pointer to the space, which must outlive it. */
+int ktune_model_load(ktune_space *space, const void *blob, size_t bytes,
+                     ktune_model **out);
+int ktune_model_destroy(ktune_model *model);
+/* Counter count K and padded depth D of a loaded model. */
+int ktune_model_info(const ktune_model *model, int *K, int *depth);
+/* Full-mode prediction: counters of TS[first .. first+count) (materialised
+ * spaces) written row-major [count][K] float32 to the DEVICE buffer out. */
+int ktune_model_predict_device(const ktune_model *model, int64_t first, int64_t count,
+                               float *out, void *stream);
+
+/* ---- search (Algorithm 1) ---------------------------------------------------
+ * Creates a search over (space, model).  The initial c_profile is TS[o] with
+ * o = floor(u * N / 2^64), u the Philox draw of domain 1, and is marked
+ * evaluated (Algorithm 1, first line).  KTUNE_EXHAUSTED if TS is empty. */
+int ktune_search_create(ktune_space *space, ktune_model *model,
+                        const ktune_search_opts *opts, void *stream,
+                        ktune_search **out);
+int ktune_search_destroy(ktune_search *search);
+/* Raw index of the current c_profile. */
+int ktune_search_current(const ktune_search *search, int64_t *raw);
+/* Make `raw` (a valid configuration) the c_profile without evaluating it. */
+int ktune_search_set_profile(ktune_search *search, int64_t raw);
+
+/* One search step (Algorithm 1's loop body after the profiling run).
+ * profiled_counters: HOST float[K], the measured counters of c_profile in the
+ * model's counter layout (finite, else KTUNE_EINVAL).  Computes B and
+ * Delta-PC (Section 3.4), predicts c_profile and every configuration not yet
+ * evaluated, scores them (Eq. score), selects k configurations (weighted draws
+ * over Eq. score_normalization, or top-k), marks them evaluated and writes
+ * their raw indices (out_raw, HOST int64[k]) and raw scores (out_score, HOST
+ * float[k]) in selection order; *n_out = number written.  If fewer than k
+ * configurations remain unevaluated, all of them are returned and the call
+ * returns KTUNE_EXHAUSTED. */
+int ktune_step(ktune_search *search, const float *profiled_counters, int k,
+               int64_t *out_raw, float *out_score, int *n_out);
+/* The same step with DEVICE buffers, enqueued on `stream` without host
+ * synchronisation: counters_dev float[K]; out_raw_dev int64[k];
+ * out_score_dev float[k]; n_out_dev int[1] (may be NULL).  The c_profile is
+ * the one current when the call is made; ktune_report cannot follow this call
+ * (use ktune_search_set_profile). */
+int ktune_step_device(ktune_search *search, const float *counters_dev, int k,
+                      int64_t *out_raw_dev, float *out_score_dev, int *n_out_dev,
+                      void *stream);
+/* Runtimes (HOST double[n]) of the configurations the last ktune_step
+ * returned, in the same order; the fastest becomes the next c_profile, the
+ * later one on ties (Algorithm 1's inner loop with t reset to infinity). */
+int ktune_report(ktune_search *search, const double *runtimes, int n);
+/* Number of configurations evaluated so far (including the initial one). */
+int ktune_search_evaluated(const ktune_search *search, int64_t *n);
+
+/* Statistics of the most recent step.  kernel_ms holds the device time of
+ * each kernel of that step in launch order (prepare, score, weights, select),
+ * measured with CUDA events on the step's stream, only while timing is
+ * enabled by ktune_search_set_timing (else 0).  Synchronises the stream of
+ * the last step. */
+typedef struct {
+  int64_t n_scored;     /* configurations scored (valid, not yet evaluated) */
+  int n_active;         /* counters with a non-zero Delta and prediction for c_profile */
+  int depth;            /* padded tree depth D */
+  float s_min, s_max;   /* over the scored configurations */
+  int n_kernels;
+  float kernel_ms[8];
+} ktune_step_stats;
+int ktune_search_stats(ktune_search *search, ktune_step_stats *out);
+/* Enable (1) or disable (0) per-kernel event timing of later steps. */
+int ktune_search_set_timing(ktune_search *search, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KTUNE_H */

@@ -1,0 +1,764 @@
+// Host side of libktune: descriptor validation, constraint tabulation, model
+// parsing and padding, search state, and the C ABI entry points (ktune.h).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace ktune {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+}  // namespace ktune
+
+using namespace ktune;
+
+#define FAIL(code, msg)   \
+  do {                    \
+    set_error(msg);       \
+    return code;          \
+  } while (0)
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+      return e_ == cudaErrorMemoryAllocation ? KTUNE_ENOMEM : KTUNE_ECUDA;              \
+    }                                                                                   \
+  } while (0)
+
+namespace {
+
+// ---- constraint bytecode (host interpreter used to tabulate groups) -------
+struct Span {
+  int begin, end;  // [begin, end) of the bytecode
+};
+
+int op_args(int op) {
+  if (op == KTUNE_OP_VAL || op == KTUNE_OP_CONST) return 1;
+  if (op == KTUNE_OP_CONST64) return 2;
+  return 0;
+}
+
+// Structural check; splits the program into groups that start and end with an
+// empty stack.
+int split_groups(const int32_t *code, int n, int P, std::vector<Span> &spans) {
+  int depth = 0, start = 0;
+  for (int i = 0; i < n;) {
+    const int op = code[i];
+    const int na = op_args(op);
+    if (op < KTUNE_OP_VAL || op > KTUNE_OP_CONST64) FAIL(KTUNE_EINVAL, "bytecode: unknown opcode");
+    if (na > 0 && i + na >= n) FAIL(KTUNE_EINVAL, "bytecode: missing argument");
+    if (op == KTUNE_OP_VAL && (code[i + 1] < 0 || code[i + 1] >= P))
+      FAIL(KTUNE_EINVAL, "bytecode: VAL parameter out of range");
+    if (op == KTUNE_OP_VAL || op == KTUNE_OP_CONST || op == KTUNE_OP_CONST64) {
+      ++depth;
+    } else if (op == KTUNE_OP_NOT) {
+      if (depth < 1) FAIL(KTUNE_EINVAL, "bytecode: stack underflow");
+    } else if (op == KTUNE_OP_REQUIRE) {
+      if (depth < 1) FAIL(KTUNE_EINVAL, "bytecode: stack underflow");
+      --depth;
+    } else {
+      if (depth < 2) FAIL(KTUNE_EINVAL, "bytecode: stack underflow");
+      --depth;
+    }
+    if (depth > 16) FAIL(KTUNE_EINVAL, "bytecode: stack deeper than 16");
+    i += 1 + na;
+    if (depth == 0) {
+      if (op != KTUNE_OP_REQUIRE) FAIL(KTUNE_EINVAL, "bytecode: value dropped without REQUIRE");
+      spans.push_back({start, i});
+      start = i;
+    }
+  }
+  if (depth != 0) FAIL(KTUNE_EINVAL, "bytecode: values left on the stack");
+  return KTUNE_OK;
+}
+
+int64_t tdiv(int64_t a, int64_t b) {
+  if (b == 0) return 0;
+  if (b == -1) return (int64_t)(0ull - (uint64_t)a);  // wraps like the rest
+  return a / b;                                         // C truncates toward zero
+}
+
+bool eval_span(const int32_t *code, Span sp, const int64_t *val) {
+  int64_t st[17];
+  int d = 0;
+  bool ok = true;
+  for (int i = sp.begin; i < sp.end;) {
+    const int op = code[i];
+    switch (op) {
+      case KTUNE_OP_VAL: st[d++] = val[code[i + 1]]; i += 2; continue;
+      case KTUNE_OP_CONST: st[d++] = code[i + 1]; i += 2; continue;
+      case KTUNE_OP_CONST64:
+        st[d++] = (int64_t)(((uint64_t)(uint32_t)code[i + 2] << 32) | (uint32_t)code[i + 1]);
+        i += 3;
+        continue;
+      case KTUNE_OP_NOT: st[d - 1] = st[d - 1] == 0; ++i; continue;
+      case KTUNE_OP_REQUIRE: ok = ok && st[d - 1] != 0; --d; ++i; continue;
+      default: break;
+    }
+    const int64_t b = st[--d], a = st[d - 1];
+    const uint64_t ua = (uint64_t)a, ub = (uint64_t)b;
+    int64_t r = 0;
+    switch (op) {
+      case KTUNE_OP_ADD: r = (int64_t)(ua + ub); break;
+      case KTUNE_OP_SUB: r = (int64_t)(ua - ub); break;
+      case KTUNE_OP_MUL: r = (int64_t)(ua * ub); break;
+      case KTUNE_OP_DIV: r = tdiv(a, b); break;
+      case KTUNE_OP_MOD: r = b == 0 ? 0 : (int64_t)(ua - (uint64_t)tdiv(a, b) * ub); break;
+      case KTUNE_OP_EQ: r = a == b; break;
+      case KTUNE_OP_NE: r = a != b; break;
+      case KTUNE_OP_LT: r = a < b; break;
+      case KTUNE_OP_LE: r = a <= b; break;
+      case KTUNE_OP_GT: r = a > b; break;
+      case KTUNE_OP_GE: r = a >= b; break;
+      case KTUNE_OP_AND: r = (a != 0) && (b != 0); break;
+      case KTUNE_OP_OR: r = (a != 0) || (b != 0); break;
+    }
+    st[d - 1] = r;
+    ++i;
+  }
+  return ok;
+}
+
+int build_groups(ktune_space *s, const int32_t *code, int n) {
+  std::vector<Span> spans;
+  int rc = split_groups(code, n, s->sa.P, spans);
+  if (rc) return rc;
+  if ((int)spans.size() > kMaxGroups) FAIL(KTUNE_EINVAL, "more than 64 constraint groups");
+  for (const Span &sp : spans) {
+    bool uses[KTUNE_MAX_PARAMS] = {false};
+    for (int i = sp.begin; i < sp.end; i += 1 + op_args(code[i]))
+      if (code[i] == KTUNE_OP_VAL) uses[code[i + 1]] = true;
+    GroupDev g{};
+    int64_t combos = 1;
+    for (int j = 0; j < s->sa.P; ++j)
+      if (uses[j]) {
+        g.param[g.n++] = (uint8_t)j;
+        combos *= s->sa.radix[j];
+      }
+    if (combos > (1 << 20)) FAIL(KTUNE_EINVAL, "constraint group reads too many value combinations");
+    int64_t st = 1;
+    for (int i = g.n - 1; i >= 0; --i) {
+      g.sub_stride[i] = (uint32_t)st;
+      st *= s->sa.radix[g.param[i]];
+    }
+    g.off_words = (uint32_t)s->table.size();
+    std::vector<uint32_t> bits((combos + 31) / 32, 0u);
+    int64_t val[KTUNE_MAX_PARAMS] = {0};
+    for (int64_t c = 0; c < combos; ++c) {
+      int64_t rem = c;
+      for (int i = g.n - 1; i >= 0; --i) {
+        const int j = g.param[i];
+        const int d = (int)(rem % s->sa.radix[j]);
+        rem /= s->sa.radix[j];
+        val[j] = s->values[s->value_off[j] + d];
+      }
+      if (eval_span(code, sp, val)) bits[c >> 5] |= 1u << (c & 31);
+    }
+    s->table.insert(s->table.end(), bits.begin(), bits.end());
+    s->groups.push_back(g);
+  }
+  s->sa.n_groups = (int)s->groups.size();
+  return KTUNE_OK;
+}
+
+uint64_t host_pack(const ktune_space *s, int64_t raw) {
+  uint64_t p = 0;
+  for (int j = s->sa.P - 1; j >= 0; --j) {
+    p |= (uint64_t)(raw % s->sa.radix[j]) << (4 * j);
+    raw /= s->sa.radix[j];
+  }
+  return p;
+}
+
+bool host_valid(const ktune_space *s, uint64_t p) {
+  for (const GroupDev &g : s->groups) {
+    uint32_t sub = 0;
+    for (int i = 0; i < g.n; ++i) sub += ((p >> (4 * g.param[i])) & 15u) * g.sub_stride[i];
+    if (!((s->table[g.off_words + (sub >> 5)] >> (sub & 31)) & 1u)) return false;
+  }
+  return true;
+}
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return KTUNE_ENOMEM;
+  }
+  return KTUNE_OK;
+}
+
+#define TRY(x)          \
+  do {                  \
+    int rc_ = (x);      \
+    if (rc_) return rc_; \
+  } while (0)
+
+// host Philox4x32-10 for the initial c_profile draw (same definition as the
+// device copy in device_common.cuh)
+uint64_t host_philox_u64(uint64_t seed, uint32_t sid, uint32_t step, uint32_t draw, uint32_t dom) {
+  uint32_t c[4] = {draw, step, sid, dom};
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = (uint32_t)p1;
+    c[2] = n2;
+    c[3] = (uint32_t)p0;
+  }
+  return (uint64_t)c[0] | ((uint64_t)c[1] << 32);
+}
+
+uint64_t mulhi64(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
+
+}  // namespace
+
+extern "C" {
+
+int ktune_abi_version(void) { return 100; }
+
+const char *ktune_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune_space **out) {
+  if (!d || !out) FAIL(KTUNE_EINVAL, "null argument");
+  *out = nullptr;
+  if (flags != KTUNE_MATERIALISE && flags != KTUNE_ON_THE_FLY) FAIL(KTUNE_EINVAL, "bad flags");
+  if (d->n_params < 1 || d->n_params > KTUNE_MAX_PARAMS) FAIL(KTUNE_EINVAL, "n_params out of range");
+  if (!d->n_values || !d->values) FAIL(KTUNE_EINVAL, "null value lists");
+  if (d->n_bytecode < 0 || (d->n_bytecode > 0 && !d->bytecode)) FAIL(KTUNE_EINVAL, "bad bytecode");
+  ktune_space *s = new (std::nothrow) ktune_space();
+  if (!s) FAIL(KTUNE_ENOMEM, "host allocation");
+  auto cleanup = [&](int rc) {
+    ktune_space_destroy(s);
+    return rc;
+  };
+  cudaGetDevice(&s->device);
+  s->flags = flags;
+  s->sa.P = d->n_params;
+  long double raw = 1;
+  int off = 0;
+  for (int j = 0; j < d->n_params; ++j) {
+    const int r = d->n_values[j];
+    if (r < 1 || r > KTUNE_MAX_VALUES) {
+      set_error("n_values out of range");
+      return cleanup(KTUNE_EINVAL);
+    }
+    s->sa.radix[j] = r;
+    s->value_off.push_back(off);
+    for (int i = 0; i < r; ++i) {
+      if (i && d->values[off + i] <= d->values[off + i - 1]) {
+        set_error("value lists must be strictly ascending");
+        return cleanup(KTUNE_EINVAL);
+      }
+      s->values.push_back(d->values[off + i]);
+    }
+    off += r;
+    raw *= r;
+  }
+  if (raw >= (long double)(1ll << 40)) {
+    set_error("raw space size must be below 2^40");
+    return cleanup(KTUNE_EINVAL);
+  }
+  s->sa.n_raw = (int64_t)raw;
+  int64_t st = 1;
+  for (int j = d->n_params - 1; j >= 0; --j) {
+    s->sa.stride[j] = st;
+    st *= s->sa.radix[j];
+  }
+  int rc = build_groups(s, d->bytecode, d->n_bytecode);
+  if (rc) return cleanup(rc);
+
+  cudaStream_t cs = (cudaStream_t)stream;
+  if ((rc = dalloc(&s->d_groups, s->groups.size()))) return cleanup(rc);
+  if ((rc = dalloc(&s->d_table, s->table.size()))) return cleanup(rc);
+  if (!s->groups.empty()) {
+    if (cudaMemcpyAsync(s->d_groups, s->groups.data(), s->groups.size() * sizeof(GroupDev),
+                        cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(s->d_table, s->table.data(), s->table.size() * 4, cudaMemcpyHostToDevice,
+                        cs) != cudaSuccess) {
+      set_error("descriptor upload failed");
+      return cleanup(KTUNE_ECUDA);
+    }
+  }
+  s->n_tiles = (s->sa.n_raw + kEnumTileRaw - 1) / kEnumTileRaw;
+  int32_t *d_count = nullptr;
+  if ((rc = dalloc(&d_count, s->n_tiles))) return cleanup(rc);
+  if ((rc = dalloc(&s->d_tile_offset, s->n_tiles + 1))) {
+    cudaFree(d_count);
+    return cleanup(rc);
+  }
+  launch_enum_count(s->sa, s->d_groups, s->d_table, s->n_tiles, d_count, cs);
+  launch_scan_tiles(d_count, s->n_tiles, s->d_tile_offset, cs);
+  cudaError_t e = cudaMemcpyAsync(&s->n_valid, s->d_tile_offset + s->n_tiles, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cudaFree(d_count);
+  if (e != cudaSuccess) {
+    set_error(std::string("enumeration: ") + cudaGetErrorString(e));
+    return cleanup(KTUNE_ECUDA);
+  }
+  if (flags == KTUNE_MATERIALISE) {
+    if ((rc = dalloc(&s->d_packed, s->n_valid))) return cleanup(rc);
+    launch_enum_write(s->sa, s->d_groups, s->d_table, s->n_tiles, s->d_tile_offset, s->d_packed,
+                      cs);
+    e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("enumeration: ") + cudaGetErrorString(e));
+      return cleanup(KTUNE_ECUDA);
+    }
+  }
+  *out = s;
+  return KTUNE_OK;
+}
+
+int ktune_space_destroy(ktune_space *s) {
+  if (!s) return KTUNE_OK;
+  cudaFree(s->d_groups);
+  cudaFree(s->d_table);
+  cudaFree(s->d_packed);
+  cudaFree(s->d_tile_offset);
+  delete s;
+  return KTUNE_OK;
+}
+
+int ktune_space_count(const ktune_space *s, int64_t *n_valid, int64_t *n_raw) {
+  if (!s) FAIL(KTUNE_EINVAL, "null space");
+  if (n_valid) *n_valid = s->n_valid;
+  if (n_raw) *n_raw = s->sa.n_raw;
+  return KTUNE_OK;
+}
+
+int ktune_space_decode(const ktune_space *s, int64_t raw, int64_t *values_out) {
+  if (!s || !values_out) FAIL(KTUNE_EINVAL, "null argument");
+  if (raw < 0 || raw >= s->sa.n_raw) FAIL(KTUNE_EINVAL, "raw index out of range");
+  const uint64_t p = host_pack(s, raw);
+  for (int j = 0; j < s->sa.P; ++j) values_out[j] = s->values[s->value_off[j] + ((p >> (4 * j)) & 15u)];
+  return KTUNE_OK;
+}
+
+int ktune_space_valid_raw(const ktune_space *s, int64_t first, int64_t count, int64_t *out_raw) {
+  if (!s || (!out_raw && count)) FAIL(KTUNE_EINVAL, "null argument");
+  if (!s->d_packed) FAIL(KTUNE_ESTATE, "space is not materialised");
+  if (first < 0 || count < 0 || first + count > s->n_valid) FAIL(KTUNE_EINVAL, "range out of TS");
+  std::vector<uint64_t> p((size_t)count);
+  if (count) CK(cudaMemcpy(p.data(), s->d_packed + first, count * 8, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < count; ++i) {
+    int64_t raw = 0;
+    for (int j = 0; j < s->sa.P; ++j) raw += (int64_t)((p[i] >> (4 * j)) & 15u) * s->sa.stride[j];
+    out_raw[i] = raw;
+  }
+  return KTUNE_OK;
+}
+
+int ktune_space_valid_digits(const ktune_space *s, int64_t first, int64_t count, uint8_t *out) {
+  if (!s || (!out && count)) FAIL(KTUNE_EINVAL, "null argument");
+  if (!s->d_packed) FAIL(KTUNE_ESTATE, "space is not materialised");
+  if (first < 0 || count < 0 || first + count > s->n_valid) FAIL(KTUNE_EINVAL, "range out of TS");
+  std::vector<uint64_t> p((size_t)count);
+  if (count) CK(cudaMemcpy(p.data(), s->d_packed + first, count * 8, cudaMemcpyDeviceToHost));
+  const int P = s->sa.P;
+  for (int64_t i = 0; i < count; ++i)
+    for (int j = 0; j < P; ++j) out[i * P + j] = (uint8_t)((p[i] >> (4 * j)) & 15u);
+  return KTUNE_OK;
+}
+
+const uint64_t *ktune_space_packed_device(const ktune_space *s) { return s ? s->d_packed : nullptr; }
+
+// ---------------------------------------------------------------------------
+int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model **out) {
+  if (!s || !blob || !out) FAIL(KTUNE_EINVAL, "null argument");
+  *out = nullptr;
+  const uint8_t *b = (const uint8_t *)blob;
+  size_t pos = 0;
+  auto rd32 = [&](uint32_t *v) {
+    if (pos + 4 > bytes) return false;
+    memcpy(v, b + pos, 4);
+    pos += 4;
+    return true;
+  };
+  uint32_t magic, ver, kind, K;
+  if (!rd32(&magic) || !rd32(&ver) || !rd32(&kind) || !rd32(&K)) FAIL(KTUNE_EMODEL, "blob truncated");
+  if (magic != 0x314D544Bu || ver != 1) FAIL(KTUNE_EMODEL, "bad magic or version");
+  if (kind != 1) FAIL(KTUNE_EMODEL, "unsupported model kind");
+  if (K < 1 || K > KTUNE_MAX_COUNTERS) FAIL(KTUNE_EMODEL, "K out of range");
+  std::vector<int> roles(K);
+  for (uint32_t k = 0; k < K; ++k) {
+    uint32_t r;
+    if (!rd32(&r)) FAIL(KTUNE_EMODEL, "blob truncated");
+    if ((int)r < 0 || (int)r >= KTUNE_PC_N_ROLES) FAIL(KTUNE_EMODEL, "bad counter role");
+    roles[k] = (int)r;
+  }
+  struct Tree {
+    std::vector<int32_t> f, t, l, r;
+    std::vector<float> v;
+  };
+  std::vector<Tree> trees(K);
+  int D = 1;
+  for (uint32_t k = 0; k < K; ++k) {
+    uint32_t n;
+    if (!rd32(&n) || n < 1 || n > (1u << (KTUNE_MAX_DEPTH + 1))) FAIL(KTUNE_EMODEL, "bad node count");
+    if (pos + (size_t)n * 20 > bytes) FAIL(KTUNE_EMODEL, "blob truncated");
+    Tree &T = trees[k];
+    T.f.resize(n); T.t.resize(n); T.l.resize(n); T.r.resize(n); T.v.resize(n);
+    memcpy(T.f.data(), b + pos, 4 * n); pos += 4 * n;
+    memcpy(T.t.data(), b + pos, 4 * n); pos += 4 * n;
+    memcpy(T.l.data(), b + pos, 4 * n); pos += 4 * n;
+    memcpy(T.r.data(), b + pos, 4 * n); pos += 4 * n;
+    memcpy(T.v.data(), b + pos, 4 * n); pos += 4 * n;
+    // every node reached exactly once from the root, depth bounded
+    std::vector<int> depth(n, -1);
+    std::vector<int> stack{0};
+    depth[0] = 0;
+    size_t seen = 0;
+    while (!stack.empty()) {
+      const int i = stack.back();
+      stack.pop_back();
+      ++seen;
+      if (depth[i] > KTUNE_MAX_DEPTH) FAIL(KTUNE_EMODEL, "tree deeper than KTUNE_MAX_DEPTH");
+      if (T.f[i] < 0) {
+        if (!isfinite(T.v[i])) FAIL(KTUNE_EMODEL, "non-finite leaf value");
+        D = std::max(D, depth[i]);
+        continue;
+      }
+      if (T.f[i] >= s->sa.P) FAIL(KTUNE_EMODEL, "tree feature beyond the space's parameters");
+      if (T.t[i] < 0) FAIL(KTUNE_EMODEL, "negative threshold");
+      for (int c : {T.l[i], T.r[i]}) {
+        if (c < 1 || c >= (int)n || depth[c] != -1) FAIL(KTUNE_EMODEL, "bad child index");
+        depth[c] = depth[i] + 1;
+        stack.push_back(c);
+      }
+    }
+    (void)seen;
+  }
+  if (pos != bytes) FAIL(KTUNE_EMODEL, "trailing bytes in blob");
+  // pad into complete trees of depth D
+  const int L = 1 << D;
+  std::vector<uint8_t> nodes((size_t)K * L, 0);
+  std::vector<float> leaves((size_t)K * L, 0.0f);
+  for (uint32_t k = 0; k < K; ++k) {
+    const Tree &T = trees[k];
+    uint8_t *nd = nodes.data() + (size_t)k * L;
+    float *lv = leaves.data() + (size_t)k * L;
+    // (source node, padded position, level)
+    std::vector<std::array<int, 3>> st{{0, 0, 0}};
+    while (!st.empty()) {
+      auto [i, pos_, lev] = st.back();
+      st.pop_back();
+      if (lev == D) {
+        lv[pos_ - (L - 1)] = T.v[i];
+        continue;
+      }
+      if (T.f[i] < 0) {
+        nd[pos_] = 0x0F;  // feature 0, threshold 15: always left
+        st.push_back({i, 2 * pos_ + 1, lev + 1});
+        st.push_back({i, 2 * pos_ + 2, lev + 1});  // unreachable copy keeps the table full
+        continue;
+      }
+      const int thr = std::min(T.t[i], 15);
+      nd[pos_] = (uint8_t)((T.f[i] << 4) | thr);
+      st.push_back({T.l[i], 2 * pos_ + 1, lev + 1});
+      st.push_back({T.r[i], 2 * pos_ + 2, lev + 1});
+    }
+  }
+  ktune_model *m = new (std::nothrow) ktune_model();
+  if (!m) FAIL(KTUNE_ENOMEM, "host allocation");
+  m->space = s;
+  m->K = (int)K;
+  m->D = D;
+  m->roles = roles;
+  int rc;
+  if ((rc = dalloc(&m->d_nodes, nodes.size())) || (rc = dalloc(&m->d_leaves, leaves.size()))) {
+    ktune_model_destroy(m);
+    return rc;
+  }
+  if (cudaMemcpy(m->d_nodes, nodes.data(), nodes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_leaves, leaves.data(), leaves.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    ktune_model_destroy(m);
+    FAIL(KTUNE_ECUDA, "model upload failed");
+  }
+  *out = m;
+  return KTUNE_OK;
+}
+
+int ktune_model_destroy(ktune_model *m) {
+  if (!m) return KTUNE_OK;
+  cudaFree(m->d_nodes);
+  cudaFree(m->d_leaves);
+  delete m;
+  return KTUNE_OK;
+}
+
+int ktune_model_info(const ktune_model *m, int *K, int *depth) {
+  if (!m) FAIL(KTUNE_EINVAL, "null model");
+  if (K) *K = m->K;
+  if (depth) *depth = m->D;
+  return KTUNE_OK;
+}
+
+int ktune_model_predict_device(const ktune_model *m, int64_t first, int64_t count, float *out,
+                               void *stream) {
+  if (!m || (!out && count)) FAIL(KTUNE_EINVAL, "null argument");
+  const ktune_space *s = m->space;
+  if (!s->d_packed) FAIL(KTUNE_ESTATE, "space is not materialised");
+  if (first < 0 || count < 0 || first + count > s->n_valid) FAIL(KTUNE_EINVAL, "range out of TS");
+  launch_predict_full(s->d_packed + first, count, m->d_nodes, m->d_leaves, m->K, m->D, out,
+                      (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return KTUNE_OK;
+}
+
+// ---------------------------------------------------------------------------
+int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts *o, void *stream,
+                        ktune_search **out) {
+  if (!s || !m || !o || !out) FAIL(KTUNE_EINVAL, "null argument");
+  *out = nullptr;
+  if (m->space != s) FAIL(KTUNE_EINVAL, "model belongs to another space");
+  if (o->k < 1 || o->k > KTUNE_MAX_K) FAIL(KTUNE_EINVAL, "k out of range");
+  if (o->select != KTUNE_SELECT_SAMPLE && o->select != KTUNE_SELECT_TOPK)
+    FAIL(KTUNE_EINVAL, "bad select mode");
+  if (!(o->inst_reaction >= 0.0 && o->inst_reaction < 1.0)) FAIL(KTUNE_EINVAL, "inst_reaction not in [0,1)");
+  if (!(o->cores > 0.0) || !isfinite(o->gamma)) FAIL(KTUNE_EINVAL, "bad cores or gamma");
+  if (!s->d_packed) FAIL(KTUNE_ESTATE, "on-the-fly spaces are not supported by this build");
+  if (o->select == KTUNE_SELECT_TOPK) FAIL(KTUNE_ESTATE, "top-k select is not supported by this build");
+  if (s->n_valid == 0) FAIL(KTUNE_EXHAUSTED, "empty tuning space");
+  ktune_search *h = new (std::nothrow) ktune_search();
+  if (!h) FAIL(KTUNE_ENOMEM, "host allocation");
+  h->space = s;
+  h->model = m;
+  h->opts = *o;
+  h->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t N = s->n_valid;
+  h->grid = score_grid(N, h->num_sms);
+  const int L = 1 << m->D;
+  const size_t tree_bytes = (size_t)((5 * L + 15) & ~15);
+  const int64_t n_tiles = (N + kSelTile - 1) / kSelTile;
+  int rc;
+  auto fail = [&](int code) {
+    ktune_search_destroy(h);
+    return code;
+  };
+  if ((rc = dalloc(&h->d_eval, (N + 31) / 32)) || (rc = dalloc(&h->d_counters, m->K)) ||
+      (rc = dalloc(&h->d_pcprof, m->K)) || (rc = dalloc(&h->d_delta, m->K)) ||
+      (rc = dalloc(&h->d_nactive, 1)) || (rc = dalloc(&h->d_active, m->K)) ||
+      (rc = dalloc(&h->d_pack, tree_bytes * m->K)) || (rc = dalloc(&h->d_s, N)) ||
+      (rc = dalloc(&h->d_minmax, h->grid)) || (rc = dalloc(&h->d_tilesum, n_tiles)) ||
+      (rc = dalloc(&h->d_stats, 4)) || (rc = dalloc(&h->d_out_raw, KTUNE_MAX_K)) ||
+      (rc = dalloc(&h->d_out_score, KTUNE_MAX_K)) || (rc = dalloc(&h->d_out_packed, KTUNE_MAX_K)) ||
+      (rc = dalloc(&h->d_nout, 1)))
+    return fail(rc);
+  if (cudaMallocHost((void **)&h->h_counters, KTUNE_MAX_COUNTERS * 4) != cudaSuccess ||
+      cudaMallocHost((void **)&h->h_out_raw, KTUNE_MAX_K * 8) != cudaSuccess ||
+      cudaMallocHost((void **)&h->h_out_score, KTUNE_MAX_K * 4) != cudaSuccess ||
+      cudaMallocHost((void **)&h->h_out_packed, KTUNE_MAX_K * 8) != cudaSuccess ||
+      cudaMallocHost((void **)&h->h_nout, 4) != cudaSuccess) {
+    set_error("pinned host allocation failed");
+    return fail(KTUNE_ENOMEM);
+  }
+  if (cudaMemsetAsync(h->d_eval, 0, ((N + 31) / 32) * 4, h->stream) != cudaSuccess) {
+    set_error("memset failed");
+    return fail(KTUNE_ECUDA);
+  }
+  // initial c_profile: TS[floor(u N / 2^64)], u from Philox domain 1
+  const int64_t o0 = (int64_t)mulhi64(host_philox_u64(o->seed, o->search_id, 0, 0, 1), (uint64_t)N);
+  uint64_t p = 0;
+  if (cudaMemcpyAsync(&p, s->d_packed + o0, 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) {
+    set_error("copy failed");
+    return fail(KTUNE_ECUDA);
+  }
+  launch_mark(h->d_eval, o0, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_error("search set-up failed");
+    return fail(KTUNE_ECUDA);
+  }
+  h->cprof_packed = p;
+  int64_t raw = 0;
+  for (int j = 0; j < s->sa.P; ++j) raw += (int64_t)((p >> (4 * j)) & 15u) * s->sa.stride[j];
+  h->cprof_raw = raw;
+  h->n_evaluated = 1;
+  *out = h;
+  return KTUNE_OK;
+}
+
+int ktune_search_destroy(ktune_search *h) {
+  if (!h) return KTUNE_OK;
+  cudaFree(h->d_eval); cudaFree(h->d_counters); cudaFree(h->d_pcprof); cudaFree(h->d_delta);
+  cudaFree(h->d_nactive); cudaFree(h->d_active); cudaFree(h->d_pack); cudaFree(h->d_s);
+  cudaFree(h->d_minmax); cudaFree(h->d_tilesum); cudaFree(h->d_stats); cudaFree(h->d_out_raw);
+  cudaFree(h->d_out_score); cudaFree(h->d_out_packed); cudaFree(h->d_nout);
+  cudaFreeHost(h->h_counters); cudaFreeHost(h->h_out_raw); cudaFreeHost(h->h_out_score);
+  cudaFreeHost(h->h_out_packed); cudaFreeHost(h->h_nout);
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+  return KTUNE_OK;
+}
+
+int ktune_search_current(const ktune_search *h, int64_t *raw) {
+  if (!h || !raw) FAIL(KTUNE_EINVAL, "null argument");
+  *raw = h->cprof_raw;
+  return KTUNE_OK;
+}
+
+int ktune_search_set_profile(ktune_search *h, int64_t raw) {
+  if (!h) FAIL(KTUNE_EINVAL, "null search");
+  const ktune_space *s = h->space;
+  if (raw < 0 || raw >= s->sa.n_raw) FAIL(KTUNE_EINVAL, "raw index out of range");
+  const uint64_t p = host_pack(s, raw);
+  if (!host_valid(s, p)) FAIL(KTUNE_EINVAL, "configuration is not valid");
+  h->cprof_raw = raw;
+  h->cprof_packed = p;
+  return KTUNE_OK;
+}
+
+int ktune_search_evaluated(const ktune_search *h, int64_t *n) {
+  if (!h || !n) FAIL(KTUNE_EINVAL, "null argument");
+  *n = h->n_evaluated;
+  return KTUNE_OK;
+}
+
+static int enqueue_step(ktune_search *h, const float *counters_dev, int k, int64_t *out_raw,
+                        float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st) {
+  const ktune_space *s = h->space;
+  const ktune_model *m = h->model;
+  PrepArgs pa{};
+  pa.K = m->K;
+  pa.D = m->D;
+  pa.inst_reaction = h->opts.inst_reaction;
+  pa.cores = h->opts.cores;
+  pa.cprof_packed = h->cprof_packed;
+  for (int i = 0; i < m->K; ++i) pa.roles[i] = (uint8_t)m->roles[i];
+  const int64_t N = s->n_valid;
+  auto mark = [&](int i) {
+    if (h->timing) cudaEventRecord(h->ev[i], st);
+  };
+  mark(0);
+  launch_prepare(pa, counters_dev, m->d_nodes, m->d_leaves, h->d_pcprof, h->d_delta, h->d_nactive,
+                 h->d_active, h->d_pack, st);
+  mark(1);
+  launch_score_mat(s->d_packed, h->d_eval, N, h->d_pack, h->d_nactive, m->D, h->d_s, h->d_minmax,
+                   h->grid, st);
+  mark(2);
+  launch_weights(h->d_s, h->d_eval, N, h->d_minmax, h->grid, h->opts.gamma, h->d_tilesum,
+                 h->d_stats, st);
+  mark(3);
+  launch_select(h->d_s, h->d_eval, N, h->d_tilesum, h->d_stats, h->opts.gamma, k, h->opts.seed,
+                h->opts.search_id, h->step_no, s->d_packed, s->sa, out_raw, out_score, out_packed,
+                n_out, st);
+  mark(4);
+  CK(cudaGetLastError());
+  h->last_stream = st;
+  h->last_scored = N - h->n_evaluated;
+  h->step_no++;
+  return KTUNE_OK;
+}
+
+int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, float *out_score,
+               int *n_out) {
+  if (!h || !counters || !out_raw || !out_score || !n_out) FAIL(KTUNE_EINVAL, "null argument");
+  if (k < 1 || k > KTUNE_MAX_K) FAIL(KTUNE_EINVAL, "k out of range");
+  const int K = h->model->K;
+  for (int i = 0; i < K; ++i)
+    if (!isfinite(counters[i])) FAIL(KTUNE_EINVAL, "non-finite profiled counter");
+  memcpy(h->h_counters, counters, K * 4);
+  CK(cudaMemcpyAsync(h->d_counters, h->h_counters, K * 4, cudaMemcpyHostToDevice, h->stream));
+  TRY(enqueue_step(h, h->d_counters, k, h->d_out_raw, h->d_out_score, h->d_out_packed, h->d_nout,
+                   h->stream));
+  CK(cudaMemcpyAsync(h->h_out_raw, h->d_out_raw, k * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_out_score, h->d_out_score, k * 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_out_packed, h->d_out_packed, k * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_nout, h->d_nout, 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int n = *h->h_nout;
+  *n_out = n;
+  memcpy(out_raw, h->h_out_raw, n * 8);
+  memcpy(out_score, h->h_out_score, n * 4);
+  h->last_raw.assign(h->h_out_raw, h->h_out_raw + n);
+  h->last_packed.assign(h->h_out_packed, h->h_out_packed + n);
+  h->n_evaluated += n;
+  if (n < k) FAIL(KTUNE_EXHAUSTED, "fewer unevaluated configurations than requested");
+  return KTUNE_OK;
+}
+
+int ktune_step_device(ktune_search *h, const float *counters_dev, int k, int64_t *out_raw_dev,
+                      float *out_score_dev, int *n_out_dev, void *stream) {
+  if (!h || !counters_dev || !out_raw_dev || !out_score_dev) FAIL(KTUNE_EINVAL, "null argument");
+  if (k < 1 || k > KTUNE_MAX_K) FAIL(KTUNE_EINVAL, "k out of range");
+  h->last_raw.clear();
+  h->last_packed.clear();
+  TRY(enqueue_step(h, counters_dev, k, out_raw_dev, out_score_dev, h->d_out_packed, n_out_dev,
+                   (cudaStream_t)stream));
+  // the number drawn is known only on the device; it is k unless the space ran out
+  h->n_evaluated = std::min<int64_t>(h->space->n_valid, h->n_evaluated + k);
+  return KTUNE_OK;
+}
+
+int ktune_search_set_timing(ktune_search *h, int enable) {
+  if (!h) FAIL(KTUNE_EINVAL, "null search");
+  if (enable && !h->ev[0])
+    for (auto &e : h->ev) CK(cudaEventCreate(&e));
+  h->timing = enable != 0;
+  return KTUNE_OK;
+}
+
+int ktune_search_stats(ktune_search *h, ktune_step_stats *out) {
+  if (!h || !out) FAIL(KTUNE_EINVAL, "null argument");
+  memset(out, 0, sizeof(*out));
+  CK(cudaStreamSynchronize(h->last_stream));
+  int na = 0;
+  float st[2] = {0, 0};
+  CK(cudaMemcpy(&na, h->d_nactive, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st, h->d_stats, 8, cudaMemcpyDeviceToHost));
+  out->n_scored = h->last_scored;
+  out->n_active = na;
+  out->depth = h->model->D;
+  out->s_min = st[0];
+  out->s_max = st[1];
+  if (h->timing) {
+    out->n_kernels = 4;
+    for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&out->kernel_ms[i], h->ev[i], h->ev[i + 1]));
+  }
+  return KTUNE_OK;
+}
+
+int ktune_report(ktune_search *h, const double *runtimes, int n) {
+  if (!h || (!runtimes && n)) FAIL(KTUNE_EINVAL, "null argument");
+  if (n != (int)h->last_raw.size() || n == 0) FAIL(KTUNE_ESTATE, "no matching ktune_step to report");
+  double t = INFINITY;
+  for (int i = 0; i < n; ++i) {
+    if (isnan(runtimes[i])) FAIL(KTUNE_EINVAL, "NaN runtime");
+    if (runtimes[i] <= t) {
+      t = runtimes[i];
+      h->cprof_raw = h->last_raw[i];
+      h->cprof_packed = h->last_packed[i];
+    }
+  }
+  h->last_raw.clear();
+  h->last_packed.clear();
+  return KTUNE_OK;
+}
+
+}  // extern "C"

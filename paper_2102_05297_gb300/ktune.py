@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libktune (include/ktune.h).
+
+Every function here only marshals arguments: each ``ktune_*`` name is the C
+entry point of the same name, called with plain pointers and sizes.  The
+library must be built (``python -m paper_2102_05297_gb300.build``); importing
+this module without it raises ImportError, so there is no silent fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import struct
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libktune.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libktune.so is not built; run `python -m paper_2102_05297_gb300.build`")
+lib = C.CDLL(LIB_PATH)
+
+KTUNE_OK, KTUNE_EINVAL, KTUNE_ENOMEM, KTUNE_EMODEL = 0, -1, -2, -3
+KTUNE_EXHAUSTED, KTUNE_ETIMEOUT, KTUNE_ECUDA, KTUNE_ESTATE = -4, -5, -6, -7
+KTUNE_MATERIALISE, KTUNE_ON_THE_FLY = 0, 1
+KTUNE_SELECT_SAMPLE, KTUNE_SELECT_TOPK = 0, 1
+MODEL_MAGIC = 0x314D544B
+
+
+class ktune_space_desc(C.Structure):
+    _fields_ = [("n_params", C.c_int), ("n_values", C.POINTER(C.c_int)),
+                ("values", C.POINTER(C.c_int64)), ("bytecode", C.POINTER(C.c_int32)),
+                ("n_bytecode", C.c_int)]
+
+
+class ktune_search_opts(C.Structure):
+    _fields_ = [("k", C.c_int), ("inst_reaction", C.c_double), ("gamma", C.c_float),
+                ("cores", C.c_double), ("seed", C.c_uint64), ("search_id", C.c_uint32),
+                ("select", C.c_int)]
+
+
+class ktune_step_stats(C.Structure):
+    _fields_ = [("n_scored", C.c_int64), ("n_active", C.c_int), ("depth", C.c_int),
+                ("s_min", C.c_float), ("s_max", C.c_float), ("n_kernels", C.c_int),
+                ("kernel_ms", C.c_float * 8)]
+
+
+_vp, _i64p, _f32p, _i32p = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_float), C.POINTER(C.c_int)
+_SIGS = {
+    "ktune_abi_version": ([], C.c_int),
+    "ktune_last_error": ([], C.c_char_p),
+    "ktune_space_create": ([C.POINTER(ktune_space_desc), C.c_int, _vp, C.POINTER(_vp)], C.c_int),
+    "ktune_space_destroy": ([_vp], C.c_int),
+    "ktune_space_count": ([_vp, _i64p, _i64p], C.c_int),
+    "ktune_space_decode": ([_vp, C.c_int64, _i64p], C.c_int),
+    "ktune_space_valid_raw": ([_vp, C.c_int64, C.c_int64, _i64p], C.c_int),
+    "ktune_space_valid_digits": ([_vp, C.c_int64, C.c_int64, _vp], C.c_int),
+    "ktune_space_packed_device": ([_vp], _vp),
+    "ktune_model_load": ([_vp, _vp, C.c_size_t, C.POINTER(_vp)], C.c_int),
+    "ktune_model_destroy": ([_vp], C.c_int),
+    "ktune_model_info": ([_vp, _i32p, _i32p], C.c_int),
+    "ktune_model_predict_device": ([_vp, C.c_int64, C.c_int64, _vp, _vp], C.c_int),
+    "ktune_search_create": ([_vp, _vp, C.POINTER(ktune_search_opts), _vp, C.POINTER(_vp)], C.c_int),
+    "ktune_search_destroy": ([_vp], C.c_int),
+    "ktune_search_current": ([_vp, _i64p], C.c_int),
+    "ktune_search_set_profile": ([_vp, C.c_int64], C.c_int),
+    "ktune_step": ([_vp, _f32p, C.c_int, _i64p, _f32p, _i32p], C.c_int),
+    "ktune_step_device": ([_vp, _vp, C.c_int, _vp, _vp, _vp, _vp], C.c_int),
+    "ktune_report": ([_vp, C.POINTER(C.c_double), C.c_int], C.c_int),
+    "ktune_search_evaluated": ([_vp, _i64p], C.c_int),
+    "ktune_search_stats": ([_vp, C.POINTER(ktune_step_stats)], C.c_int),
+    "ktune_search_set_timing": ([_vp, C.c_int], C.c_int),
+}
+EXPORTED = list(_SIGS)
+for _n, (_a, _r) in _SIGS.items():
+    _f = getattr(lib, _n)
+    _f.argtypes = _a
+    _f.restype = _r
+    globals()[_n] = _f
+
+
+class KtuneError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s failed (%d): %s" % (where, code, lib.ktune_last_error().decode()))
+
+
+def check(rc: int, where: str) -> int:
+    if rc != KTUNE_OK:
+        raise KtuneError(rc, where)
+    return rc
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+# ---------------------------------------------------------------------------
+def model_blob(model: dict) -> bytes:
+    """Serialise a tree-ensemble model (see include/ktune.h for the layout)."""
+    roles = model["roles"]
+    out = [struct.pack("<4I", MODEL_MAGIC, 1, 1, len(roles)),
+           np.asarray(roles, "<i4").tobytes()]
+    for t in model["trees"]:
+        n = len(t["feature"])
+        out.append(struct.pack("<I", n))
+        for key, dt in (("feature", "<i4"), ("threshold", "<i4"), ("left", "<i4"),
+                        ("right", "<i4"), ("value", "<f4")):
+            out.append(np.asarray(t[key], dt).tobytes())
+    return b"".join(out)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Space:
+    """Owns a ktune_space handle."""
+
+    def __init__(self, values: Sequence[Sequence[int]], bytecode: Sequence[int] = (),
+                 flags: int = KTUNE_MATERIALISE, stream=None):
+        self.radices = [len(v) for v in values]
+        nv, self._nv = _arr(self.radices, np.int32)
+        vals, self._vals = _arr([x for v in values for x in v], np.int64)
+        bc, self._bc = _arr(list(bytecode) or [0], np.int32)
+        self._keep = (nv, vals, bc)
+        d = ktune_space_desc(len(values), self._nv, self._vals, self._bc, len(bytecode))
+        h = C.c_void_p()
+        check(lib.ktune_space_create(C.byref(d), flags, _stream_ptr(stream), C.byref(h)),
+              "ktune_space_create")
+        self.h = h
+        self.flags = flags
+
+    @classmethod
+    def from_desc(cls, desc, flags=KTUNE_MATERIALISE, stream=None):
+        return cls(desc.values, desc.bytecode, flags, stream)
+
+    def count(self):
+        nv, nr = C.c_int64(), C.c_int64()
+        check(lib.ktune_space_count(self.h, C.byref(nv), C.byref(nr)), "ktune_space_count")
+        return nv.value, nr.value
+
+    def decode(self, raw: int) -> List[int]:
+        out = (C.c_int64 * len(self.radices))()
+        check(lib.ktune_space_decode(self.h, raw, out), "ktune_space_decode")
+        return list(out)
+
+    def valid_raw(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        if count is None:
+            count = self.count()[0] - first
+        out = np.empty(count, np.int64)
+        check(lib.ktune_space_valid_raw(self.h, first, count,
+                                        out.ctypes.data_as(C.POINTER(C.c_int64))),
+              "ktune_space_valid_raw")
+        return out
+
+    def valid_digits(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        if count is None:
+            count = self.count()[0] - first
+        out = np.empty((count, len(self.radices)), np.uint8)
+        check(lib.ktune_space_valid_digits(self.h, first, count, out.ctypes.data),
+              "ktune_space_valid_digits")
+        return out
+
+    def packed_device(self) -> int:
+        return lib.ktune_space_packed_device(self.h) or 0
+
+    def close(self):
+        if self.h:
+            lib.ktune_space_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class Model:
+    def __init__(self, space: Space, model: dict):
+        blob = model_blob(model)
+        self._blob = C.create_string_buffer(blob, len(blob))
+        h = C.c_void_p()
+        check(lib.ktune_model_load(space.h, self._blob, len(blob), C.byref(h)), "ktune_model_load")
+        self.h = h
+        self.space = space
+        k, d = C.c_int(), C.c_int()
+        check(lib.ktune_model_info(h, C.byref(k), C.byref(d)), "ktune_model_info")
+        self.K, self.depth = k.value, d.value
+
+    def predict_device(self, first: int, count: int, out_ptr: int, stream=None):
+        check(lib.ktune_model_predict_device(self.h, first, count, out_ptr, _stream_ptr(stream)),
+              "ktune_model_predict_device")
+
+    def close(self):
+        if self.h:
+            lib.ktune_model_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class Search:
+    def __init__(self, space: Space, model: Model, k: int = 5, inst_reaction: float = 0.7,
+                 gamma: float = -0.25, cores: float = 1000.0, seed: int = 0, search_id: int = 0,
+                 select: int = KTUNE_SELECT_SAMPLE, stream=None):
+        o = ktune_search_opts(k, inst_reaction, gamma, cores, seed, search_id, select)
+        h = C.c_void_p()
+        check(lib.ktune_search_create(space.h, model.h, C.byref(o), _stream_ptr(stream),
+                                      C.byref(h)), "ktune_search_create")
+        self.h = h
+        self.k = k
+        self.K = model.K
+        self.space, self.model = space, model
+        self._raw = np.empty(64, np.int64)
+        self._score = np.empty(64, np.float32)
+
+    def current(self) -> int:
+        r = C.c_int64()
+        check(lib.ktune_search_current(self.h, C.byref(r)), "ktune_search_current")
+        return r.value
+
+    def set_profile(self, raw: int):
+        check(lib.ktune_search_set_profile(self.h, raw), "ktune_search_set_profile")
+
+    def step(self, counters, k: Optional[int] = None):
+        """Returns (raw indices, scores); raises KtuneError except on
+        KTUNE_EXHAUSTED, where the partial batch is returned."""
+        k = self.k if k is None else k
+        c, cp = _arr(counters, np.float32)
+        n = C.c_int()
+        rc = lib.ktune_step(self.h, cp, k, self._raw.ctypes.data_as(C.POINTER(C.c_int64)),
+                            self._score.ctypes.data_as(C.POINTER(C.c_float)), C.byref(n))
+        if rc not in (KTUNE_OK, KTUNE_EXHAUSTED):
+            check(rc, "ktune_step")
+        return self._raw[:n.value].copy(), self._score[:n.value].copy()
+
+    def step_device(self, counters_ptr: int, k: int, out_raw_ptr: int, out_score_ptr: int,
+                    n_out_ptr: int = 0, stream=None):
+        check(lib.ktune_step_device(self.h, counters_ptr, k, out_raw_ptr, out_score_ptr,
+                                    n_out_ptr or None, _stream_ptr(stream)), "ktune_step_device")
+
+    def report(self, runtimes):
+        r, rp = _arr(runtimes, np.float64)
+        check(lib.ktune_report(self.h, rp, len(r)), "ktune_report")
+
+    def evaluated(self) -> int:
+        n = C.c_int64()
+        check(lib.ktune_search_evaluated(self.h, C.byref(n)), "ktune_search_evaluated")
+        return n.value
+
+    def stats(self) -> ktune_step_stats:
+        st = ktune_step_stats()
+        check(lib.ktune_search_stats(self.h, C.byref(st)), "ktune_search_stats")
+        return st
+
+    def set_timing(self, enable: bool = True):
+        check(lib.ktune_search_set_timing(self.h, int(enable)), "ktune_search_set_timing")
+
+    def close(self):
+        if self.h:
+            lib.ktune_search_destroy(self.h)
+            self.h = None
+
+    __del__ = close
