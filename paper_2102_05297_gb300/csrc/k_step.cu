@@ -114,50 +114,69 @@ __device__ void expert_system(const float *cnt, const uint8_t *roles, int K, dou
   }
 }
 
+// Grid (K, leaf chunks): every CTA predicts c_profile for all K counters
+// (one thread per tree) and runs the expert system on one thread; CTA (p, c)
+// then writes chunk c of counter p's node bytes and term table into slot
+// rank(p) of the pack, where rank counts the active counters before p.
+constexpr int kPrepLeaves = 2048;  // leaves per CTA (8 per thread)
+
 __global__ void __launch_bounds__(256) k_prepare(PrepArgs pa, const float *counters,
-                                                 const uint8_t *nodes, const float *leaves,
+                                                 const uint8_t *__restrict__ nodes,
+                                                 const float *__restrict__ leaves,
                                                  float *pcprof_out, float *delta_out,
                                                  int *n_active_out, int *active_out,
                                                  uint8_t *pack) {
   __shared__ float pcprof[KTUNE_MAX_COUNTERS], delta[KTUNE_MAX_COUNTERS];
-  __shared__ int active[KTUNE_MAX_COUNTERS];
-  __shared__ int n_active;
   const int L = 1 << pa.D;
   const int tree_bytes = (5 * L + 15) & ~15;
-  if (threadIdx.x < pa.K) {
-    const int p = threadIdx.x;
-    const uint32_t leaf = tree_leaf(nodes + (size_t)p * L, pa.D, pa.cprof_packed);
-    pcprof[p] = leaves[(size_t)p * L + leaf];
+  const int p = blockIdx.x;
+  if ((int)threadIdx.x < pa.K) {
+    const int q = threadIdx.x;
+    const uint32_t leaf = tree_leaf(nodes + (size_t)q * L, pa.D, pa.cprof_packed);
+    pcprof[q] = leaves[(size_t)q * L + leaf];
   }
-  if (threadIdx.x == 0) expert_system(counters, pa.roles, pa.K, pa.inst_reaction, pa.cores, delta);
+  if (threadIdx.x == blockDim.x - 1)
+    expert_system(counters, pa.roles, pa.K, pa.inst_reaction, pa.cores, delta);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int n = 0;
-    for (int p = 0; p < pa.K; ++p)
-      if (delta[p] != 0.0f && pcprof[p] != 0.0f) active[n++] = p;
-    n_active = n;
-    *n_active_out = n;
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    if (threadIdx.x < pa.K) {
+      pcprof_out[threadIdx.x] = pcprof[threadIdx.x];
+      delta_out[threadIdx.x] = delta[threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int q = 0; q < pa.K; ++q)
+        if (delta[q] != 0.0f && pcprof[q] != 0.0f) active_out[n++] = q;
+      *n_active_out = n;
+    }
   }
-  if (threadIdx.x < pa.K) {
-    pcprof_out[threadIdx.x] = pcprof[threadIdx.x];
-    delta_out[threadIdx.x] = delta[threadIdx.x];
+  if (!(delta[p] != 0.0f && pcprof[p] != 0.0f)) return;
+  int rank = 0;
+  for (int q = 0; q < p; ++q) rank += (delta[q] != 0.0f && pcprof[q] != 0.0f) ? 1 : 0;
+  uint8_t *dst = pack + (size_t)rank * tree_bytes;
+  float *terms = reinterpret_cast<float *>(dst + L);
+  const uint8_t *src = nodes + (size_t)p * L;
+  const float *lv = leaves + (size_t)p * L;
+  const float A = pcprof[p], dl = delta[p];
+  constexpr int PER = kPrepLeaves / 256;
+  float x[PER];
+  uint8_t nb[PER];
+  const int base = blockIdx.y * kPrepLeaves + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = base + j * 256;
+    x[j] = i < L ? __ldg(lv + i) : 0.0f;
+    nb[j] = i < L ? __ldg(src + i) : 0;
   }
-  __syncthreads();
-  if (threadIdx.x < n_active) active_out[threadIdx.x] = active[threadIdx.x];
-  // pack: per active counter, its node bytes then its term table
-  for (int a = 0; a < n_active; ++a) {
-    const int p = active[a];
-    uint8_t *dst = pack + (size_t)a * tree_bytes;
-    const uint8_t *src = nodes + (size_t)p * L;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
-    float *terms = reinterpret_cast<float *>(dst + L);
-    const float A = pcprof[p], dl = delta[p];
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-      const float x = leaves[(size_t)p * L + i];
-      const float den = __fadd_rn(x, A);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = base + j * 256;
+    if (i < L) {
+      const float den = __fadd_rn(x[j], A);
       float t = 0.0f;
-      if (x != 0.0f && den != 0.0f) t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(x, A), den));
+      if (x[j] != 0.0f && den != 0.0f) t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(x[j], A), den));
       terms[i] = t;
+      dst[i] = nb[j];
     }
   }
 }
@@ -463,8 +482,10 @@ __global__ void k_mark(uint32_t *ev, int64_t ordinal) {
 void launch_prepare(const PrepArgs &pa, const float *counters, const uint8_t *nodes,
                     const float *leaves, float *pcprof, float *delta32, int *n_active,
                     int *active, uint8_t *pack, cudaStream_t st) {
-  k_prepare<<<1, 256, 0, st>>>(pa, counters, nodes, leaves, pcprof, delta32, n_active, active,
-                               pack);
+  const int L = 1 << pa.D;
+  dim3 grid(pa.K, (L + kPrepLeaves - 1) / kPrepLeaves);
+  k_prepare<<<grid, 256, 0, st>>>(pa, counters, nodes, leaves, pcprof, delta32, n_active, active,
+                                  pack);
 }
 
 int score_grid(int64_t N, int num_sms) {

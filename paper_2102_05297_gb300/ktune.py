@@ -171,7 +171,7 @@ class Space:
         return lib.ktune_space_packed_device(self.h) or 0
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             lib.ktune_space_destroy(self.h)
             self.h = None
 
@@ -195,7 +195,7 @@ class Model:
               "ktune_model_predict_device")
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             lib.ktune_model_destroy(self.h)
             self.h = None
 
@@ -260,7 +260,7 @@ class Search:
         check(lib.ktune_search_set_timing(self.h, int(enable)), "ktune_search_set_timing")
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             lib.ktune_search_destroy(self.h)
             self.h = None
 
