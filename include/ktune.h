@@ -233,6 +233,47 @@ int ktune_search_stats(ktune_search *search, ktune_step_stats *out);
 /* Enable (1) or disable (0) per-kernel event timing of later steps. */
 int ktune_search_set_timing(ktune_search *search, int enable);
 
+/* ---- scoring without device allocation ------------------------------------
+ * No counterpart in the paper: this is a deployment convenience.
+ *
+ * Some callers cannot allocate device memory: for example a plugin whose host
+ * framework owns all device memory and forbids allocation inside its execute
+ * callback, or a latency-critical loop that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  They cannot create the
+ * handles above (creation allocates), so this call takes only device buffers
+ * the caller owns and allocates nothing itself (no cudaMalloc, no cudaFree).
+ *
+ * It computes, for the step with measured counters `counters_dev` and profiled
+ * configuration `cprof_packed`, Eq. score of every configuration of TS:
+ *   packed_dev     device uint64[n], TS in ktune's packed form (digit j in bits
+ *                  4j..4j+3), n >= 1
+ *   evaluated_dev  device uint32[ceil(n/32)], bit i set = TS[i] already evaluated
+ *   nodes_dev      device uint8[K][2^depth] padded complete trees: node i has
+ *                  children 2i+1 (left) and 2i+2 (right), byte = feature << 4 |
+ *                  threshold, right iff digit(feature) > threshold
+ *   leaves_dev     device float[K][2^depth] leaf values of those trees
+ *   roles          HOST int32[K] counter roles (KTUNE_PC_*)
+ *   counters_dev   device float[K] measured counters of c_profile
+ *   scores_dev     device float[n] out: Eq. score, 0 for evaluated entries
+ *   minmax_dev     device float[2] out: min and max score over unevaluated
+ *                  entries (+inf / -inf when there are none)
+ * The results equal those of the scoring inside ktune_step.
+ *
+ * Working memory is one fixed 1 MiB array compiled into the library and held
+ * on every GPU that loads it until the process exits.  Sizes beyond it are
+ * rejected with KTUNE_EINVAL: K * 5 * 2^depth bytes (rounded up to 16) must not
+ * exceed 1 MiB - 16 KiB (K <= 40 at depth 12).  The first call on each device
+ * looks up the array's device address once (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other threads) race and give
+ * undefined results, so serialise them.  Enqueued on `stream` (cudaStream_t),
+ * without host synchronisation. */
+int ktune_score_noalloc(const uint64_t *packed_dev, int64_t n, const uint32_t *evaluated_dev,
+                        const uint8_t *nodes_dev, const float *leaves_dev, int K, int depth,
+                        const int32_t *roles, const float *counters_dev, uint64_t cprof_packed,
+                        double inst_reaction, double cores, float *scores_dev,
+                        float *minmax_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

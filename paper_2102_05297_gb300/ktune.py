@@ -70,6 +70,8 @@ _SIGS = {
     "ktune_search_evaluated": ([_vp, _i64p], C.c_int),
     "ktune_search_stats": ([_vp, C.POINTER(ktune_step_stats)], C.c_int),
     "ktune_search_set_timing": ([_vp, C.c_int], C.c_int),
+    "ktune_score_noalloc": ([_vp, C.c_int64, _vp, _vp, _vp, C.c_int, C.c_int, _i32p, _vp,
+                             C.c_uint64, C.c_double, C.c_double, _vp, _vp, _vp], C.c_int),
 }
 EXPORTED = list(_SIGS)
 for _n, (_a, _r) in _SIGS.items():
