@@ -286,6 +286,17 @@ int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune
   }
   int rc = build_groups(s, d->bytecode, d->n_bytecode);
   if (rc) return cleanup(rc);
+  {  // narrow layout: ceil(log2 radix) bits per digit, parameter 0 lowest
+    int bits = 0;
+    for (int j = 0; j < d->n_params; ++j) {
+      int w = 1;
+      while ((1 << w) < s->sa.radix[j]) ++w;
+      s->pos[j] = (uint8_t)std::min(bits, 255);
+      s->width[j] = (uint8_t)w;
+      bits += w;
+    }
+    s->narrow = bits <= 32;
+  }
 
   cudaStream_t cs = (cudaStream_t)stream;
   if ((rc = dalloc(&s->d_groups, s->groups.size()))) return cleanup(rc);
@@ -320,6 +331,12 @@ int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune
     if ((rc = dalloc(&s->d_packed, s->n_valid))) return cleanup(rc);
     launch_enum_write(s->sa, s->d_groups, s->d_table, s->n_tiles, s->d_tile_offset, s->d_packed,
                       cs);
+    if (s->narrow) {
+      if ((rc = dalloc(&s->d_narrow, s->n_valid))) return cleanup(rc);
+      PrepArgs lay{};
+      for (int j = 0; j < s->sa.P; ++j) lay.pos[j] = s->pos[j];
+      launch_narrow_pack(s->d_packed, s->n_valid, lay, s->d_narrow, cs);
+    }
     e = cudaStreamSynchronize(cs);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -336,6 +353,7 @@ int ktune_space_destroy(ktune_space *s) {
   cudaFree(s->d_groups);
   cudaFree(s->d_table);
   cudaFree(s->d_packed);
+  cudaFree(s->d_narrow);
   cudaFree(s->d_tile_offset);
   delete s;
   return KTUNE_OK;
@@ -553,8 +571,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t N = s->n_valid;
   h->grid = score_grid(N, h->num_sms);
-  const int L = 1 << m->D;
-  const size_t tree_bytes = (size_t)((5 * L + 15) & ~15);
+  const size_t tree_bytes = (size_t)pack_tree_bytes(m->D, s->narrow);
   const int64_t n_tiles = (N + kSelTile - 1) / kSelTile;
   int rc;
   auto fail = [&](int code) {
@@ -651,6 +668,12 @@ static int enqueue_step(ktune_search *h, const float *counters_dev, int k, int64
   pa.cores = h->opts.cores;
   pa.cprof_packed = h->cprof_packed;
   for (int i = 0; i < m->K; ++i) pa.roles[i] = (uint8_t)m->roles[i];
+  pa.narrow = s->narrow ? 1 : 0;
+  for (int j = 0; j < s->sa.P; ++j) {
+    pa.pos[j] = s->pos[j];
+    pa.width[j] = s->width[j];
+    pa.radix[j] = (uint8_t)s->sa.radix[j];
+  }
   const int64_t N = s->n_valid;
   auto mark = [&](int i) {
     if (h->timing) cudaEventRecord(h->ev[i], st);
@@ -659,8 +682,12 @@ static int enqueue_step(ktune_search *h, const float *counters_dev, int k, int64
   launch_prepare(pa, counters_dev, m->d_nodes, m->d_leaves, h->d_pcprof, h->d_delta, h->d_nactive,
                  h->d_active, h->d_pack, st);
   mark(1);
-  launch_score_mat(s->d_packed, h->d_eval, N, h->d_pack, h->d_nactive, m->D, h->d_s, h->d_minmax,
-                   h->grid, st);
+  if (s->narrow)
+    launch_score_narrow(s->d_narrow, h->d_eval, N, h->d_pack, h->d_nactive, m->D, h->d_s,
+                        h->d_minmax, h->grid, st);
+  else
+    launch_score_mat(s->d_packed, h->d_eval, N, h->d_pack, h->d_nactive, m->D, h->d_s,
+                     h->d_minmax, h->grid, st);
   mark(2);
   launch_weights(h->d_s, h->d_eval, N, h->d_minmax, h->grid, h->opts.gamma, h->d_tilesum,
                  h->d_stats, st);

@@ -45,7 +45,19 @@ struct PrepArgs {
   double cores;
   uint64_t cprof_packed;
   uint8_t roles[KTUNE_MAX_COUNTERS];
+  // narrow layout (digit j in bits pos[j] .. pos[j]+width[j]-1 of one 32-bit word):
+  // when set, the pack holds 32-bit node words instead of node bytes
+  int narrow;
+  uint8_t pos[KTUNE_MAX_PARAMS];
+  uint8_t width[KTUNE_MAX_PARAMS];
+  uint8_t radix[KTUNE_MAX_PARAMS];
 };
+
+// Bytes of one active tree in the step's pack (node bytes or node words, then terms).
+__host__ __device__ inline int pack_tree_bytes(int D, bool narrow) {
+  const int L = 1 << D;
+  return narrow ? 8 * L : ((5 * L + 15) & ~15);
+}
 
 // ---- enumeration (k_space.cu) ----
 void launch_enum_count(const SpaceArgs &sa, const GroupDev *groups, const uint32_t *table,
@@ -71,6 +83,11 @@ void launch_select(const float *s, uint32_t *evaluated, int64_t N, uint64_t *til
                    const float *stats, float gamma, int k, uint64_t seed, uint32_t search_id,
                    uint32_t step, const uint64_t *packed, SpaceArgs sa, int64_t *out_raw,
                    float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st);
+void launch_narrow_pack(const uint64_t *packed, int64_t n, const PrepArgs &layout,
+                        uint32_t *narrow, cudaStream_t st);
+void launch_score_narrow(const uint32_t *narrow, const uint32_t *evaluated, int64_t N,
+                         const uint8_t *pack, const int *n_active, int D, float *s,
+                         float2 *minmax, int grid, cudaStream_t st);
 void launch_predict_full(const uint64_t *packed, int64_t count, const uint8_t *nodes,
                          const float *leaves, int K, int D, float *out, cudaStream_t st);
 void launch_mark(uint32_t *evaluated, int64_t ordinal, cudaStream_t st);
@@ -93,6 +110,9 @@ struct ktune_space {
   ktune::GroupDev *d_groups = nullptr;
   uint32_t *d_table = nullptr;
   uint64_t *d_packed = nullptr;      // materialised TS
+  bool narrow = false;               // all digits fit one 32-bit word
+  uint8_t pos[KTUNE_MAX_PARAMS] = {0}, width[KTUNE_MAX_PARAMS] = {0};
+  uint32_t *d_narrow = nullptr;      // TS in the narrow layout (materialised, narrow spaces)
   int64_t *d_tile_offset = nullptr;  // exclusive valid prefix per raw tile (+ total)
 };
 

@@ -114,6 +114,22 @@ __device__ void expert_system(const float *cnt, const uint8_t *roles, int K, dou
   }
 }
 
+// Node word of the narrow walk for node byte (feature f, threshold t):
+// low 5 bits = s, the left shift that brings digit f to the top of the word;
+// top byte = 255 - T8 with T8 = ((t + 1) << (8 - w)) - 1, or 0 when the
+// configuration can never go right (t >= radix - 1, pass-through nodes).
+// For x = W << s the carry out of x + word is set exactly when the digit
+// exceeds t: the top byte of x is the digit followed by 8 - w bits of the
+// next digits (< 2^(8-w)), and s only fills low bits of x that are zero.
+__device__ __forceinline__ uint32_t narrow_word(uint32_t nb, const PrepArgs &pa) {
+  const int f = nb >> 4, t = nb & 15;
+  const int w = pa.width[f];
+  const uint32_t s = 32u - pa.pos[f] - w;
+  uint32_t c8 = 0;
+  if (t < pa.radix[f] - 1) c8 = 255u - ((((uint32_t)t + 1u) << (8 - w)) - 1u);
+  return (c8 << 24) | s;
+}
+
 // Grid (K, leaf chunks): every CTA predicts c_profile for all K counters
 // (one thread per tree) and runs the expert system on one thread; CTA (p, c)
 // then writes chunk c of counter p's node bytes and term table into slot
@@ -128,7 +144,7 @@ __global__ void __launch_bounds__(256) k_prepare(PrepArgs pa, const float *count
                                                  uint8_t *pack) {
   __shared__ float pcprof[KTUNE_MAX_COUNTERS], delta[KTUNE_MAX_COUNTERS];
   const int L = 1 << pa.D;
-  const int tree_bytes = (5 * L + 15) & ~15;
+  const int tree_bytes = pack_tree_bytes(pa.D, pa.narrow != 0);
   const int p = blockIdx.x;
   if ((int)threadIdx.x < pa.K) {
     const int q = threadIdx.x;
@@ -154,7 +170,8 @@ __global__ void __launch_bounds__(256) k_prepare(PrepArgs pa, const float *count
   int rank = 0;
   for (int q = 0; q < p; ++q) rank += (delta[q] != 0.0f && pcprof[q] != 0.0f) ? 1 : 0;
   uint8_t *dst = pack + (size_t)rank * tree_bytes;
-  float *terms = reinterpret_cast<float *>(dst + L);
+  float *terms = reinterpret_cast<float *>(dst + (pa.narrow ? 4 * L : L));
+  uint32_t *words = reinterpret_cast<uint32_t *>(dst);
   const uint8_t *src = nodes + (size_t)p * L;
   const float *lv = leaves + (size_t)p * L;
   const float A = pcprof[p], dl = delta[p];
@@ -176,7 +193,13 @@ __global__ void __launch_bounds__(256) k_prepare(PrepArgs pa, const float *count
       float t = 0.0f;
       if (x[j] != 0.0f && den != 0.0f) t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(x[j], A), den));
       terms[i] = t;
-      dst[i] = nb[j];
+      if (!pa.narrow) {
+        dst[i] = nb[j];
+      } else if (i + 1 < L) {
+        words[i + 1] = narrow_word(nb[j], pa);  // 1-based heap slot of node i
+      } else {
+        words[0] = 0;
+      }
     }
   }
 }
@@ -278,6 +301,120 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     }
     minmax[blockIdx.x] = make_float2(mn, mx);
   }
+}
+
+// ---- narrow score path (all digits in one 32-bit word) --------------------
+// One node visit: x = W << s (funnel shift by the word's low 5 bits), the
+// carry of x + word is "digit > threshold", and j = 2 j + carry moves to the
+// child in the 1-based heap.  Trees are staged group by group; a CTA runs its
+// whole range through one group before staging the next, keeping the partial
+// score in s_out between groups (same float32 value, same summation order).
+__device__ __forceinline__ uint32_t narrow_visit(uint32_t j, uint32_t word, uint32_t W) {
+  const uint32_t x = __funnelshift_l(0u, W, word);
+  uint32_t sum;
+  asm("add.cc.u32 %0, %2, %3;\n\tmadc.lo.u32 %1, %1, 2, 0;" : "=r"(sum), "+r"(j) : "r"(x), "r"(word));
+  return j;
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(kScoreThreads, 1)
+    k_score_narrow(const uint32_t *__restrict__ narrow, const uint32_t *__restrict__ evaluated,
+                   int64_t N, const uint8_t *__restrict__ pack, const int *__restrict__ n_active_ptr,
+                   int D, float *__restrict__ s_out, float2 *__restrict__ minmax) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ float red_mn[kScoreThreads / 32], red_mx[kScoreThreads / 32];
+  const int n_active = *n_active_ptr;
+  const int L = 1 << D;
+  const int tree_bytes = 8 * L;
+  const int per_group = max(1, kSmemBudget / tree_bytes);
+  const int n_groups = max(1, (n_active + per_group - 1) / per_group);
+  const int64_t lo = N * (int64_t)blockIdx.x / gridDim.x;
+  const int64_t hi = N * (int64_t)(blockIdx.x + 1) / gridDim.x;
+  float mn = FLT_MAX, mx = -FLT_MAX;
+  bool any = false;
+  for (int g = 0; g < n_groups; ++g) {
+    const int t0 = g * per_group;
+    const int nt = max(0, min(per_group, n_active - t0));
+    if (g) __syncthreads();
+    {
+      const uint4 *src = reinterpret_cast<const uint4 *>(pack + (size_t)t0 * tree_bytes);
+      uint4 *dst = reinterpret_cast<uint4 *>(smem);
+      const int n16 = nt * tree_bytes / 16;
+      for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const bool first = g == 0, last = g == n_groups - 1;
+    for (int64_t base = lo; base < hi; base += (int64_t)kScoreThreads * CPT) {
+      uint32_t W[CPT];
+      float s[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int64_t i = base + (int64_t)c * kScoreThreads + threadIdx.x;
+        W[c] = i < hi ? __ldg(narrow + i) : 0u;
+        s[c] = (first || i >= hi) ? 0.0f : s_out[i];
+      }
+      for (int a = 0; a < nt; ++a) {
+        const uint32_t *words = reinterpret_cast<const uint32_t *>(smem + (size_t)a * tree_bytes);
+        const float *terms = reinterpret_cast<const float *>(smem + (size_t)a * tree_bytes + 4 * L);
+        uint32_t j[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) j[c] = 1u;
+        for (int l = 0; l < D; ++l) {
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], words[j[c]], W[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) s[c] = __fadd_rn(s[c], terms[j[c] - (uint32_t)L]);
+      }
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int64_t i = base + (int64_t)c * kScoreThreads + threadIdx.x;
+        if (i < hi) {
+          if (last) {
+            const bool ev = (__ldg(evaluated + (i >> 5)) >> (i & 31)) & 1u;
+            s_out[i] = ev ? 0.0f : s[c];
+            if (!ev) {
+              mn = fminf(mn, s[c]);
+              mx = fmaxf(mx, s[c]);
+              any = true;
+            }
+          } else {
+            s_out[i] = s[c];
+          }
+        }
+      }
+    }
+  }
+  if (!any) {
+    mn = INFINITY;
+    mx = -INFINITY;
+  }
+  for (int o = 16; o; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_mn[threadIdx.x >> 5] = mn;
+    red_mx[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kScoreThreads / 32; ++w) {
+      mn = fminf(mn, red_mn[w]);
+      mx = fmaxf(mx, red_mx[w]);
+    }
+    minmax[blockIdx.x] = make_float2(mn, mx);
+  }
+}
+
+__global__ void k_narrow_pack(const uint64_t *__restrict__ packed, int64_t n, PrepArgs lay,
+                              uint32_t *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t p = packed[i];
+  uint32_t w = 0;
+  for (int j = 0; j < KTUNE_MAX_PARAMS; ++j) w |= nib64(p, j) << lay.pos[j];
+  out[i] = w;
 }
 
 // ---- normalisation and weights ---------------------------------------------
@@ -506,6 +643,25 @@ void launch_score_mat(const uint64_t *packed, const uint32_t *evaluated, int64_t
   }
   k_score_mat<kScoreCPT><<<grid, kScoreThreads, kSmemBudget, st>>>(packed, evaluated, N, pack,
                                                                    n_active, D, s, minmax);
+}
+
+void launch_score_narrow(const uint32_t *narrow, const uint32_t *evaluated, int64_t N,
+                         const uint8_t *pack, const int *n_active, int D, float *s, float2 *minmax,
+                         int grid, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_score_narrow<kScoreCPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSmemBudget);
+    attr = true;
+  }
+  k_score_narrow<kScoreCPT><<<grid, kScoreThreads, kSmemBudget, st>>>(narrow, evaluated, N, pack,
+                                                                      n_active, D, s, minmax);
+}
+
+void launch_narrow_pack(const uint64_t *packed, int64_t n, const PrepArgs &layout, uint32_t *narrow,
+                        cudaStream_t st) {
+  if (n == 0) return;
+  k_narrow_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(packed, n, layout, narrow);
 }
 
 void launch_weights(const float *s, const uint32_t *evaluated, int64_t N, const float2 *minmax,

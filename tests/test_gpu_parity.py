@@ -247,3 +247,18 @@ def test_full_size_mid_space_steps(kt):
     gpu, cnt, rt = _synthetic(d, roles, 0)
     out = run_pair(d, model, cnt, steps=3, k=5, seed=0, runtime_fn=rt, kt=kt)
     _check(out)
+
+
+def test_steps_wide_space_general_path(kt):
+    """Eleven 5-valued parameters need 33 bits in the one-word layout, so this
+    space takes the general (two-word) walk."""
+    values = [[1, 2, 3, 4, 5]] * 11
+    code = []
+    for j in range(0, 10, 2):
+        code += W.c_sum_le([j, j + 1], 3)
+    d = W.SpaceDesc("wide", ["p%d" % j for j in range(11)], values, code)
+    roles = W.layout(16)
+    model = random_model(d.radices, roles, depth=9, seed=33)
+    gpu, cnt, rt = _synthetic(d, roles, 5)
+    out = run_pair(d, model, cnt, steps=4, k=5, seed=3, runtime_fn=rt, kt=kt)
+    _check(out)
