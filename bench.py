@@ -165,19 +165,21 @@ def run_ours(args):
     wl, desc, roles, gpu, sp, valid, digits, model, m = setup(kt, name, seed)
     K, Wu = args.steps, args.warmup
     traj = record(kt, sp, m, gpu, valid, digits, wl, seed, Wu + K)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: steps on a non-default stream run as one captured CUDA graph
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     # ---- device-resident timed steps -------------------------------------
     s = kt.Search(sp, m, k=wl["k"], seed=seed, stream=stream)
     s.set_timing(True)
-    cnt_dev = torch.tensor(np.stack([t[1] for t in traj]), dtype=torch.float32, device="cuda")
+    cnt_host = [np.ascontiguousarray(t[1], dtype=np.float32) for t in traj]
     out_raw = torch.empty(wl["k"], dtype=torch.int64, device="cuda")
     out_sc = torch.empty(wl["k"], dtype=torch.float32, device="cuda")
     n_out = torch.empty(1, dtype=torch.int32, device="cuda")
     for i in range(Wu):
         s.set_profile(int(traj[i][0]))
-        s.step_device(cnt_dev[i].data_ptr(), wl["k"], out_raw.data_ptr(), out_sc.data_ptr(),
+        s.step_device(cnt_host[i], wl["k"], out_raw.data_ptr(), out_sc.data_ptr(),
                       n_out.data_ptr(), stream)
     torch.cuda.synchronize()
     if dist:
@@ -190,7 +192,7 @@ def run_ours(args):
         flush.zero_()
         s.set_profile(int(traj[i][0]))
         e0.record(stream)
-        s.step_device(cnt_dev[i].data_ptr(), wl["k"], out_raw.data_ptr(), out_sc.data_ptr(),
+        s.step_device(cnt_host[i], wl["k"], out_raw.data_ptr(), out_sc.data_ptr(),
                       n_out.data_ptr(), stream)
         e1.record(stream)
         st = s.stats()                  # synchronises

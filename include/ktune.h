@@ -201,12 +201,16 @@ int ktune_search_set_profile(ktune_search *search, int64_t raw);
  * returns KTUNE_EXHAUSTED. */
 int ktune_step(ktune_search *search, const float *profiled_counters, int k,
                int64_t *out_raw, float *out_score, int *n_out);
-/* The same step with DEVICE buffers, enqueued on `stream` without host
- * synchronisation: counters_dev float[K]; out_raw_dev int64[k];
- * out_score_dev float[k]; n_out_dev int[1] (may be NULL).  The c_profile is
- * the one current when the call is made; ktune_report cannot follow this call
- * (use ktune_search_set_profile). */
-int ktune_step_device(ktune_search *search, const float *counters_dev, int k,
+/* The same step with DEVICE output buffers, enqueued on `stream` without
+ * host synchronisation.  profiled_counters: HOST float[K] as for ktune_step
+ * (the bottleneck analysis and Delta-PC are O(K) scalar work done on the host
+ * in float64; the step's kernels receive Delta with their launch
+ * parameters, so the host buffer may be reused when the call returns);
+ * out_raw_dev int64[k]; out_score_dev float[k]; n_out_dev int[1] (may be
+ * NULL).  The c_profile is the one current when the call is made;
+ * ktune_report cannot follow this call (use ktune_search_set_profile).  On a
+ * non-default stream the step runs as one CUDA graph launch. */
+int ktune_step_device(ktune_search *search, const float *profiled_counters, int k,
                       int64_t *out_raw_dev, float *out_score_dev, int *n_out_dev,
                       void *stream);
 /* Runtimes (HOST double[n]) of the configurations the last ktune_step

@@ -231,6 +231,82 @@ uint64_t mulhi64(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128
 
 }  // namespace
 
+namespace ktune {
+
+// Section 3.4: bottlenecks (Eqs. global-read, global-write, local,
+// inst_fitted, fp32 and its analogues, maxutil, issue, paral) and the
+// Delta-PC reaction (memory: -b; instructions: Eq. fp32_reaction; parallelism:
+// +b).  Float64, each formula left to right as printed; percentages read as
+// pct / 100; ins_util = min(1, ISSUE_U / 50); bottlenecks clamped to [0, 1],
+// Deltas to [-1, 1]; absent counters take neutral values (LOC_O and the
+// optional instruction classes 0, SM_E = WARP_E = WARP_NP_E = 100, no thread
+// count => no parallelism bottleneck); RT + WT = 0 => memory bottlenecks 0;
+// ins_fitted = 0 => instruction fractions 0; WARP_E or WARP_NP_E = 0 count as
+// 100.  Built with -ffp-contract=off: no fused multiply-add.
+void host_expert(const int *roles, int K, const float *cnt, double r, double cores,
+                 float *delta32) {
+  double v[KTUNE_PC_N_ROLES] = {0};
+  bool has[KTUNE_PC_N_ROLES] = {false};
+  v[KTUNE_PC_SM_E] = v[KTUNE_PC_WARP_E] = v[KTUNE_PC_WARP_NP_E] = 100.0;
+  for (int k = 0; k < K; ++k) {
+    const int ro = roles[k];
+    if (ro < KTUNE_PC_INERT && !has[ro]) {
+      has[ro] = true;
+      v[ro] = (double)cnt[k];
+    }
+  }
+  auto clamp01 = [](double x) { return std::min(1.0, std::max(0.0, x)); };
+  auto react = [&](double b) { return b <= r ? 0.0 : -((b - r) / (1.0 - r)); };
+  double D[KTUNE_PC_N_ROLES] = {0};
+  auto mem = [&](int rt, int wt, int u) {
+    const double a = v[rt], b = v[wt], util = v[u];
+    double br = 0.0, bw = 0.0;
+    if (a + b > 0.0) {
+      br = clamp01(a / (a + b) * (util / 100.0));
+      bw = clamp01(b / (a + b) * (util / 100.0));
+    }
+    D[rt] = -br;
+    D[wt] = -bw;
+  };
+  mem(KTUNE_PC_DRAM_RT, KTUNE_PC_DRAM_WT, KTUNE_PC_DRAM_U);
+  mem(KTUNE_PC_L2_RT, KTUNE_PC_L2_WT, KTUNE_PC_L2_U);
+  mem(KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT, KTUNE_PC_SHR_U);
+  D[KTUNE_PC_TEX_RWT] = -clamp01(v[KTUNE_PC_TEX_U] / 100.0);
+  D[KTUNE_PC_LOC_O] = -clamp01(v[KTUNE_PC_LOC_O] / 100.0 *
+                               std::max(std::max(v[KTUNE_PC_DRAM_U] / 100.0, v[KTUNE_PC_L2_U] / 100.0),
+                                        v[KTUNE_PC_TEX_U] / 100.0));
+  double we = v[KTUNE_PC_WARP_E], wn = v[KTUNE_PC_WARP_NP_E];
+  if (we == 0.0) we = 100.0;
+  if (wn == 0.0) wn = 100.0;
+  const double ins_fitted = 32.0 * v[KTUNE_PC_INST_EXE] * (100.0 / we) * (100.0 / wn);
+  const double issue_u = v[KTUNE_PC_INST_ISSUE_U];
+  const double ins_util = std::min(1.0, issue_u / 50.0);
+  const int cls[7] = {KTUNE_PC_INST_F32, KTUNE_PC_INST_F64, KTUNE_PC_INST_INT, KTUNE_PC_INST_MISC,
+                      KTUNE_PC_INST_LDST, KTUNE_PC_INST_CONT, KTUNE_PC_INST_BCONV};
+  double util_max = 0.0;
+  for (int c = 0; c < 7; ++c) {
+    const double frac = ins_fitted > 0.0 ? v[cls[c]] / ins_fitted : 0.0;
+    util_max = c == 0 ? frac : std::max(util_max, frac);
+    D[cls[c]] = react(clamp01(frac * ins_util));
+  }
+  D[KTUNE_PC_INST_ISSUE_U] = react(clamp01(util_max * ((100.0 - issue_u) / 100.0)));
+  D[KTUNE_PC_SM_E] = clamp01((100.0 - v[KTUNE_PC_SM_E]) / 100.0);
+  if (has[KTUNE_PC_GLOBAL])
+    D[KTUNE_PC_GLOBAL] = clamp01(std::max(0.0, (cores * 5.0 - v[KTUNE_PC_GLOBAL]) / (cores * 5.0)));
+  bool seen[KTUNE_PC_N_ROLES] = {false};
+  for (int k = 0; k < K; ++k) {
+    const int ro = roles[k];
+    float d = 0.0f;
+    if (ro < KTUNE_PC_INERT && !seen[ro]) {
+      seen[ro] = true;
+      d = (float)std::min(1.0, std::max(-1.0, D[ro]));
+    }
+    delta32[k] = d;
+  }
+}
+
+}  // namespace ktune
+
 extern "C" {
 
 int ktune_abi_version(void) { return 100; }
@@ -326,6 +402,14 @@ int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune
   if (e != cudaSuccess) {
     set_error(std::string("enumeration: ") + cudaGetErrorString(e));
     return cleanup(KTUNE_ECUDA);
+  }
+  if (flags == KTUNE_ON_THE_FLY) {
+    s->tile_offset.resize(s->n_tiles + 1);
+    if (cudaMemcpy(s->tile_offset.data(), s->d_tile_offset, (s->n_tiles + 1) * 8,
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+      set_error("tile offsets copy failed");
+      return cleanup(KTUNE_ECUDA);
+    }
   }
   if (flags == KTUNE_MATERIALISE) {
     if ((rc = dalloc(&s->d_packed, s->n_valid))) return cleanup(rc);
@@ -557,22 +641,42 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
     FAIL(KTUNE_EINVAL, "bad select mode");
   if (!(o->inst_reaction >= 0.0 && o->inst_reaction < 1.0)) FAIL(KTUNE_EINVAL, "inst_reaction not in [0,1)");
   if (!(o->cores > 0.0) || !isfinite(o->gamma)) FAIL(KTUNE_EINVAL, "bad cores or gamma");
-  if (!s->d_packed) FAIL(KTUNE_ESTATE, "on-the-fly spaces are not supported by this build");
-  if (o->select == KTUNE_SELECT_TOPK) FAIL(KTUNE_ESTATE, "top-k select is not supported by this build");
   if (s->n_valid == 0) FAIL(KTUNE_EXHAUSTED, "empty tuning space");
+  const bool otf = s->flags == KTUNE_ON_THE_FLY;
+  if (otf && !s->narrow)
+    FAIL(KTUNE_ESTATE, "on-the-fly spaces need all digits in one 32-bit word (sum of ceil(log2 n_values) <= 32)");
+  if (otf && s->sa.n_raw >= (int64_t)1 << 32) FAIL(KTUNE_EINVAL, "on-the-fly spaces need fewer than 2^32 raw configurations");
+  const int64_t N = s->n_valid;
+  if (N >= ((int64_t)1 << 32) - 1) FAIL(KTUNE_EINVAL, "more than 2^32 - 2 valid configurations");
+  const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
+  if ((n_sub + kSuper - 1) / kSuper > kMaxSuper) FAIL(KTUNE_EINVAL, "space too large for the select hierarchy");
   ktune_search *h = new (std::nothrow) ktune_search();
   if (!h) FAIL(KTUNE_ENOMEM, "host allocation");
   h->space = s;
   h->model = m;
   h->opts = *o;
   h->stream = (cudaStream_t)stream;
+  h->mode = otf ? 2 : (s->narrow ? 0 : 1);
+  h->n_sub = n_sub;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t N = s->n_valid;
-  h->grid = score_grid(N, h->num_sms);
-  const size_t tree_bytes = (size_t)pack_tree_bytes(m->D, s->narrow);
-  const int64_t n_tiles = (N + kSelTile - 1) / kSelTile;
+  // work items: one contiguous range per SM
+  std::vector<ItemDev> items;
+  {
+    const int64_t units = otf ? s->n_tiles : N;
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(h->num_sms, otf ? units : (units + 4095) / 4096));
+    for (int64_t b = 0; b < G; ++b) {
+      ItemDev it{};
+      it.search = 0;
+      it.lo = units * b / G;
+      it.hi = units * (b + 1) / G;
+      if (it.hi > it.lo) items.push_back(it);
+    }
+  }
+  h->n_items = (int)items.size();
+  h->grid = h->n_items;
+  const size_t tree_bytes = (size_t)pack_tree_bytes(m->D, h->mode != 1);
   int rc;
   auto fail = [&](int code) {
     ktune_search_destroy(h);
@@ -580,12 +684,15 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   };
   if ((rc = dalloc(&h->d_eval, (N + 31) / 32)) || (rc = dalloc(&h->d_counters, m->K)) ||
       (rc = dalloc(&h->d_pcprof, m->K)) || (rc = dalloc(&h->d_delta, m->K)) ||
-      (rc = dalloc(&h->d_nactive, 1)) || (rc = dalloc(&h->d_active, m->K)) ||
-      (rc = dalloc(&h->d_pack, tree_bytes * m->K)) || (rc = dalloc(&h->d_s, N)) ||
-      (rc = dalloc(&h->d_minmax, h->grid)) || (rc = dalloc(&h->d_tilesum, n_tiles)) ||
-      (rc = dalloc(&h->d_stats, 4)) || (rc = dalloc(&h->d_out_raw, KTUNE_MAX_K)) ||
-      (rc = dalloc(&h->d_out_score, KTUNE_MAX_K)) || (rc = dalloc(&h->d_out_packed, KTUNE_MAX_K)) ||
-      (rc = dalloc(&h->d_nout, 1)))
+      (rc = dalloc(&h->d_nactive, 1)) || (rc = dalloc(&h->d_pack, tree_bytes * m->K)) ||
+      (rc = dalloc(&h->d_s, N)) || (rc = dalloc(&h->d_w, N)) || (rc = dalloc(&h->d_subsum, n_sub)) ||
+      (rc = dalloc(&h->d_supsum, (n_sub + kSuper - 1) / kSuper)) ||
+      (rc = dalloc(&h->d_cand_key, (size_t)h->n_items * KTUNE_MAX_K)) ||
+      (rc = dalloc(&h->d_cand_raw, (size_t)h->n_items * KTUNE_MAX_K)) || (rc = dalloc(&h->d_mm, 2)) ||
+      (rc = dalloc(&h->d_srch, 1)) || (rc = dalloc(&h->d_steps, 1)) ||
+      (rc = dalloc(&h->d_items, h->n_items)) || (rc = dalloc(&h->d_sub_search, n_sub)) ||
+      (rc = dalloc(&h->d_out_raw, KTUNE_MAX_K)) || (rc = dalloc(&h->d_out_score, KTUNE_MAX_K)) ||
+      (rc = dalloc(&h->d_out_packed, KTUNE_MAX_K)) || (rc = dalloc(&h->d_nout, 1)))
     return fail(rc);
   if (cudaMallocHost((void **)&h->h_counters, KTUNE_MAX_COUNTERS * 4) != cudaSuccess ||
       cudaMallocHost((void **)&h->h_out_raw, KTUNE_MAX_K * 8) != cudaSuccess ||
@@ -595,41 +702,108 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
     set_error("pinned host allocation failed");
     return fail(KTUNE_ENOMEM);
   }
-  if (cudaMemsetAsync(h->d_eval, 0, ((N + 31) / 32) * 4, h->stream) != cudaSuccess) {
-    set_error("memset failed");
+  SearchDev &sd = h->sdh;
+  sd.packed = s->d_packed;
+  sd.narrow = s->d_narrow;
+  sd.tile_offset = s->d_tile_offset;
+  sd.groups = s->d_groups;
+  sd.table = s->d_table;
+  sd.N = N;
+  sd.mode = h->mode;
+  sd.select = o->select;
+  sd.sa = s->sa;
+  for (int j = 0; j < KTUNE_MAX_PARAMS; ++j) {
+    sd.pos[j] = s->pos[j];
+    sd.width[j] = s->width[j];
+  }
+  sd.nodes = m->d_nodes;
+  sd.leaves = m->d_leaves;
+  sd.K = m->K;
+  sd.D = m->D;
+  for (int i = 0; i < m->K; ++i) sd.roles[i] = (uint8_t)m->roles[i];
+  sd.inst_reaction = o->inst_reaction;
+  sd.cores = o->cores;
+  sd.gamma = o->gamma;
+  sd.search_id = o->search_id;
+  sd.seed = o->seed;
+  sd.eval = h->d_eval;
+  sd.pack = h->d_pack;
+  sd.pcprof = h->d_pcprof;
+  sd.delta = h->d_delta;
+  sd.n_active = h->d_nactive;
+  sd.mm = h->d_mm;
+  sd.s = h->d_s;
+  sd.w = h->d_w;
+  sd.sub_sum = h->d_subsum;
+  sd.super_sum = h->d_supsum;
+  sd.cand_key = h->d_cand_key;
+  sd.cand_raw = h->d_cand_raw;
+  sd.item_begin = 0;
+  sd.item_end = h->n_items;
+  sd.sub_begin = 0;
+  cudaStream_t cs = h->stream;
+  if (cudaMemcpyAsync(h->d_srch, &sd, sizeof(sd), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(ItemDev),
+                      cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+      cudaMemsetAsync(h->d_sub_search, 0, n_sub * sizeof(int), cs) != cudaSuccess ||
+      cudaMemsetAsync(h->d_eval, 0, ((N + 31) / 32) * 4, cs) != cudaSuccess) {
+    set_error("search set-up upload failed");
     return fail(KTUNE_ECUDA);
   }
   // initial c_profile: TS[floor(u N / 2^64)], u from Philox domain 1
   const int64_t o0 = (int64_t)mulhi64(host_philox_u64(o->seed, o->search_id, 0, 0, 1), (uint64_t)N);
-  uint64_t p = 0;
-  if (cudaMemcpyAsync(&p, s->d_packed + o0, 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) {
-    set_error("copy failed");
-    return fail(KTUNE_ECUDA);
+  int64_t raw = -1;
+  if (!otf) {
+    uint64_t p = 0;
+    if (cudaMemcpyAsync(&p, s->d_packed + o0, 8, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess) {
+      set_error("copy failed");
+      return fail(KTUNE_ECUDA);
+    }
+    raw = 0;
+    for (int j = 0; j < s->sa.P; ++j) raw += (int64_t)((p >> (4 * j)) & 15u) * s->sa.stride[j];
+  } else {
+    const std::vector<int64_t> &to = s->tile_offset;
+    const int64_t t = (int64_t)(std::upper_bound(to.begin(), to.end(), o0) - to.begin()) - 1;
+    int64_t rank = o0 - to[t];
+    for (int64_t r = t * kEnumTileRaw; r < std::min<int64_t>(s->sa.n_raw, (t + 1) * kEnumTileRaw); ++r)
+      if (host_valid(s, host_pack(s, r)) && rank-- == 0) {
+        raw = r;
+        break;
+      }
   }
-  launch_mark(h->d_eval, o0, h->stream);
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+  launch_mark(h->d_eval, o0, cs);
+  if (raw < 0 || cudaStreamSynchronize(cs) != cudaSuccess) {
     set_error("search set-up failed");
     return fail(KTUNE_ECUDA);
   }
-  h->cprof_packed = p;
-  int64_t raw = 0;
-  for (int j = 0; j < s->sa.P; ++j) raw += (int64_t)((p >> (4 * j)) & 15u) * s->sa.stride[j];
   h->cprof_raw = raw;
+  h->cprof_packed = host_pack(s, raw);
   h->n_evaluated = 1;
   *out = h;
   return KTUNE_OK;
 }
 
+static void drop_graph(ktune_search *h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->prep_node = nullptr;
+}
+
 int ktune_search_destroy(ktune_search *h) {
   if (!h) return KTUNE_OK;
-  cudaFree(h->d_eval); cudaFree(h->d_counters); cudaFree(h->d_pcprof); cudaFree(h->d_delta);
-  cudaFree(h->d_nactive); cudaFree(h->d_active); cudaFree(h->d_pack); cudaFree(h->d_s);
-  cudaFree(h->d_minmax); cudaFree(h->d_tilesum); cudaFree(h->d_stats); cudaFree(h->d_out_raw);
-  cudaFree(h->d_out_score); cudaFree(h->d_out_packed); cudaFree(h->d_nout);
-  cudaFreeHost(h->h_counters); cudaFreeHost(h->h_out_raw); cudaFreeHost(h->h_out_score);
-  cudaFreeHost(h->h_out_packed); cudaFreeHost(h->h_nout);
+  void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
+                 h->d_s, h->d_w, h->d_subsum, h->d_supsum, h->d_cand_key, h->d_cand_raw, h->d_mm, h->d_srch,
+                 h->d_steps, h->d_items, h->d_sub_search, h->d_out_raw, h->d_out_score,
+                 h->d_out_packed, h->d_nout};
+  for (void *p : dev) cudaFree(p);
+  void *pin[] = {h->h_counters, h->h_out_raw, h->h_out_score, h->h_out_packed, h->h_nout};
+  for (void *p : pin) cudaFreeHost(p);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
+  drop_graph(h);
   delete h;
   return KTUNE_OK;
 }
@@ -657,48 +831,87 @@ int ktune_search_evaluated(const ktune_search *h, int64_t *n) {
   return KTUNE_OK;
 }
 
-static int enqueue_step(ktune_search *h, const float *counters_dev, int k, int64_t *out_raw,
-                        float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st) {
-  const ktune_space *s = h->space;
+// The kernels of one step, in order (recorded into a graph or launched).
+static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStream_t st,
+                                bool capturing) {
   const ktune_model *m = h->model;
-  PrepArgs pa{};
-  pa.K = m->K;
-  pa.D = m->D;
-  pa.inst_reaction = h->opts.inst_reaction;
-  pa.cores = h->opts.cores;
-  pa.cprof_packed = h->cprof_packed;
-  for (int i = 0; i < m->K; ++i) pa.roles[i] = (uint8_t)m->roles[i];
-  pa.narrow = s->narrow ? 1 : 0;
-  for (int j = 0; j < s->sa.P; ++j) {
-    pa.pos[j] = s->pos[j];
-    pa.width[j] = s->width[j];
-    pa.radix[j] = (uint8_t)s->sa.radix[j];
-  }
-  const int64_t N = s->n_valid;
+  // while capturing, external records become event nodes of the graph
   auto mark = [&](int i) {
-    if (h->timing) cudaEventRecord(h->ev[i], st);
+    if (!h->timing) return;
+    if (capturing) cudaEventRecordWithFlags(h->ev[i], st, cudaEventRecordExternal);
+    else cudaEventRecord(h->ev[i], st);
   };
   mark(0);
-  launch_prepare(pa, counters_dev, m->d_nodes, m->d_leaves, h->d_pcprof, h->d_delta, h->d_nactive,
-                 h->d_active, h->d_pack, st);
+  launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
   mark(1);
-  if (s->narrow)
-    launch_score_narrow(s->d_narrow, h->d_eval, N, h->d_pack, h->d_nactive, m->D, h->d_s,
-                        h->d_minmax, h->grid, st);
-  else
-    launch_score_mat(s->d_packed, h->d_eval, N, h->d_pack, h->d_nactive, m->D, h->d_s,
-                     h->d_minmax, h->grid, st);
+  launch_bscore(h->d_srch, h->d_steps, h->d_items, h->n_items, h->mode,
+                h->opts.select == KTUNE_SELECT_TOPK, h->grid, st);
   mark(2);
-  launch_weights(h->d_s, h->d_eval, N, h->d_minmax, h->grid, h->opts.gamma, h->d_tilesum,
-                 h->d_stats, st);
+  if (h->opts.select == KTUNE_SELECT_SAMPLE) launch_bweights(h->d_srch, h->d_sub_search, h->n_sub, st);
   mark(3);
-  launch_select(h->d_s, h->d_eval, N, h->d_tilesum, h->d_stats, h->opts.gamma, k, h->opts.seed,
-                h->opts.search_id, h->step_no, s->d_packed, s->sa, out_raw, out_score, out_packed,
-                n_out, st);
+  launch_bselect(h->d_srch, h->d_steps, 1, st);
   mark(4);
+}
+
+// Capture the step into a graph once per (stream, timing mode); later steps
+// only replace the prepare kernel's by-value step parameters and relaunch.
+static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st) {
+  if (h->gexec && (h->graph_stream != st || h->graph_timing != h->timing)) drop_graph(h);
+  if (!h->gexec) {
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    launch_step_kernels(h, sb, st, true);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture(st, &g));
+    h->graph = g;
+    size_t n = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CK(cudaGraphGetNodes(g, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      CK(cudaGraphNodeGetType(nd, &t));
+      if (t != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp{};
+      CK(cudaGraphKernelNodeGetParams(nd, &kp));
+      if (kp.func == bprep_func<1>()) h->prep_node = nd;
+    }
+    if (!h->prep_node) FAIL(KTUNE_ECUDA, "graph capture lost the prepare kernel");
+    CK(cudaGraphInstantiate(&h->gexec, g, 0));
+    h->graph_stream = st;
+    h->graph_timing = h->timing;
+  } else {
+    cudaKernelNodeParams kp{};
+    CK(cudaGraphKernelNodeGetParams(h->prep_node, &kp));
+    void *args[] = {&h->d_srch, &h->d_steps, &sb};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CK(cudaGraphExecKernelNodeSetParams(h->gexec, h->prep_node, &kp));
+  }
+  CK(cudaGraphLaunch(h->gexec, st));
+  return KTUNE_OK;
+}
+
+static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *out_raw,
+                        float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st) {
+  StepBatch<1> sb{};
+  StepDev &sp = sb.st[0];
+  sp.cprof_packed = h->cprof_packed;
+  host_expert(h->model->roles.data(), h->model->K, counters, h->opts.inst_reaction, h->opts.cores,
+              sp.delta);
+  sp.out_raw = out_raw;
+  sp.out_score = out_score;
+  sp.out_packed = out_packed;
+  sp.n_out = n_out;
+  sp.step = h->step_no;
+  sp.k = k;
+  if (st != nullptr && h->use_graph) {
+    TRY(launch_step_graph(h, sb, st));
+  } else {
+    launch_step_kernels(h, sb, st, false);
+  }
   CK(cudaGetLastError());
   h->last_stream = st;
-  h->last_scored = N - h->n_evaluated;
+  h->last_scored = h->space->n_valid - h->n_evaluated;
   h->step_no++;
   return KTUNE_OK;
 }
@@ -710,9 +923,7 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
   const int K = h->model->K;
   for (int i = 0; i < K; ++i)
     if (!isfinite(counters[i])) FAIL(KTUNE_EINVAL, "non-finite profiled counter");
-  memcpy(h->h_counters, counters, K * 4);
-  CK(cudaMemcpyAsync(h->d_counters, h->h_counters, K * 4, cudaMemcpyHostToDevice, h->stream));
-  TRY(enqueue_step(h, h->d_counters, k, h->d_out_raw, h->d_out_score, h->d_out_packed, h->d_nout,
+  TRY(enqueue_step(h, counters, k, h->d_out_raw, h->d_out_score, h->d_out_packed, h->d_nout,
                    h->stream));
   CK(cudaMemcpyAsync(h->h_out_raw, h->d_out_raw, k * 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_out_score, h->d_out_score, k * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -730,13 +941,15 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
   return KTUNE_OK;
 }
 
-int ktune_step_device(ktune_search *h, const float *counters_dev, int k, int64_t *out_raw_dev,
+int ktune_step_device(ktune_search *h, const float *counters, int k, int64_t *out_raw_dev,
                       float *out_score_dev, int *n_out_dev, void *stream) {
-  if (!h || !counters_dev || !out_raw_dev || !out_score_dev) FAIL(KTUNE_EINVAL, "null argument");
+  if (!h || !counters || !out_raw_dev || !out_score_dev) FAIL(KTUNE_EINVAL, "null argument");
   if (k < 1 || k > KTUNE_MAX_K) FAIL(KTUNE_EINVAL, "k out of range");
+  for (int i = 0; i < h->model->K; ++i)
+    if (!isfinite(counters[i])) FAIL(KTUNE_EINVAL, "non-finite profiled counter");
   h->last_raw.clear();
   h->last_packed.clear();
-  TRY(enqueue_step(h, counters_dev, k, out_raw_dev, out_score_dev, h->d_out_packed, n_out_dev,
+  TRY(enqueue_step(h, counters, k, out_raw_dev, out_score_dev, h->d_out_packed, n_out_dev,
                    (cudaStream_t)stream));
   // the number drawn is known only on the device; it is k unless the space ran out
   h->n_evaluated = std::min<int64_t>(h->space->n_valid, h->n_evaluated + k);
@@ -756,14 +969,21 @@ int ktune_search_stats(ktune_search *h, ktune_step_stats *out) {
   memset(out, 0, sizeof(*out));
   CK(cudaStreamSynchronize(h->last_stream));
   int na = 0;
-  float st[2] = {0, 0};
+  int mm[2] = {0, 0};
   CK(cudaMemcpy(&na, h->d_nactive, 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(st, h->d_stats, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(mm, h->d_mm, 8, cudaMemcpyDeviceToHost));
+  auto inv = [](int k) {
+    const int b = k >= 0 ? k : k ^ 0x7FFFFFFF;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+  };
   out->n_scored = h->last_scored;
   out->n_active = na;
   out->depth = h->model->D;
-  out->s_min = st[0];
-  out->s_max = st[1];
+  const bool none = mm[0] == 0x7FFFFFFF && mm[1] == (int)0x80000000;
+  out->s_min = none ? INFINITY : inv(mm[0]);
+  out->s_max = none ? -INFINITY : inv(mm[1]);
   if (h->timing) {
     out->n_kernels = 4;
     for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&out->kernel_ms[i], h->ev[i], h->ev[i + 1]));

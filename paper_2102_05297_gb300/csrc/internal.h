@@ -59,6 +59,91 @@ __host__ __device__ inline int pack_tree_bytes(int D, bool narrow) {
   return narrow ? 8 * L : ((5 * L + 15) & ~15);
 }
 
+// ---- batched step (k_batch.cu): one launch of each kernel serves S searches ----
+constexpr int kSubTile = 1024;          // configurations per weight sub-tile
+constexpr int kSuper = 32;              // sub-tiles per super-tile (select hierarchy)
+constexpr int kMaxSuper = 4096;         // => at most 134M valid configurations per search
+constexpr int kOtfRun = 4;              // raw indices per thread per decode round (on-the-fly)
+
+// Static description of one search, uploaded once.
+struct SearchDev {
+  const uint64_t *packed;     // materialised TS, nibble layout (or null)
+  const uint32_t *narrow;     // materialised TS, one-word layout (or null)
+  const int64_t *tile_offset; // valid prefix per raw tile of kEnumTileRaw (on-the-fly)
+  const GroupDev *groups;
+  const uint32_t *table;
+  int64_t N;                  // valid configurations
+  int mode;                   // 0 materialised one-word, 1 materialised nibble, 2 on-the-fly one-word
+  int select;                 // KTUNE_SELECT_*
+  SpaceArgs sa;
+  uint8_t pos[KTUNE_MAX_PARAMS], width[KTUNE_MAX_PARAMS];
+  const uint8_t *nodes;
+  const float *leaves;
+  int K, D;
+  uint8_t roles[KTUNE_MAX_COUNTERS];
+  double inst_reaction, cores;
+  float gamma;
+  uint32_t search_id;
+  uint64_t seed;
+  // scratch owned by the search
+  uint32_t *eval;             // bit per TS ordinal
+  uint8_t *pack;              // per step: active trees' nodes + terms
+  float *pcprof, *delta;      // [K]
+  int *n_active;
+  int *mm;                    // ordered-int min and max of the unevaluated scores
+  float *s;                   // [N] scores (partial sums between tree groups)
+  uint32_t *w;                // [N] integer weights (sample mode)
+  uint64_t *sub_sum;          // [ceil(N / kSubTile)]
+  uint64_t *super_sum;        // [ceil(N / (kSubTile * kSuper))], zeroed by the prepare kernel
+  uint64_t *cand_key;         // [items][k] top-k keys
+  int64_t *cand_raw;          // [items][k]
+  int64_t item_begin, item_end, sub_begin;
+};
+
+// Per-step inputs and outputs of one search.
+struct StepDev {
+  uint64_t cprof_packed;
+  int64_t *out_raw;
+  float *out_score;
+  uint64_t *out_packed;
+  int *n_out;
+  uint32_t step;
+  int k;
+  float delta[KTUNE_MAX_COUNTERS];   // Delta-PC per counter slot (float32)
+};
+
+// A work item of the score kernel: a range of TS ordinals (materialised) or
+// of raw tiles (on-the-fly) of one search.
+struct ItemDev {
+  int search;
+  int pad;
+  int64_t lo, hi;
+};
+
+constexpr int kMaxBatch = 64;           // searches per batched launch
+template <int NB>
+struct StepBatch {
+  StepDev st[NB];
+};
+// steps_in (by value) is written to steps_dev by the prepare kernel, so the
+// host buffer can be reused as soon as the call returns.
+template <int NB>
+void launch_bprep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<NB> &steps_in, int S,
+                  int K_max, int D_max, cudaStream_t st);
+template <int NB>
+const void *bprep_func();
+
+// Bottleneck analysis and Delta-PC (Section 3.4) on the host, float64 with
+// the operation order of the equations; Delta per counter slot as float32.
+void host_expert(const int *roles, int K, const float *counters, double inst_reaction,
+                 double cores, float *delta32);
+int bscore_threads();
+void launch_bscore(const SearchDev *srch, const StepDev *steps, const ItemDev *items, int n_items,
+                   int mode, bool topk, int grid, cudaStream_t st);
+void launch_bweights(const SearchDev *srch, const int *sub_search, int64_t n_sub_total,
+                     cudaStream_t st);
+void launch_bselect(const SearchDev *srch, const StepDev *steps, int S, cudaStream_t st);
+
 // ---- enumeration (k_space.cu) ----
 void launch_enum_count(const SpaceArgs &sa, const GroupDev *groups, const uint32_t *table,
                        int64_t n_tiles, int32_t *tile_count, cudaStream_t st);
@@ -76,18 +161,8 @@ int score_grid(int64_t N, int num_sms);
 void launch_score_mat(const uint64_t *packed, const uint32_t *evaluated, int64_t N,
                       const uint8_t *pack, const int *n_active, int D, float *s,
                       float2 *minmax, int grid, cudaStream_t st);
-void launch_weights(const float *s, const uint32_t *evaluated, int64_t N, const float2 *minmax,
-                    int n_part, float gamma, uint64_t *tile_sum, float *stats,
-                    cudaStream_t st);
-void launch_select(const float *s, uint32_t *evaluated, int64_t N, uint64_t *tile_sum,
-                   const float *stats, float gamma, int k, uint64_t seed, uint32_t search_id,
-                   uint32_t step, const uint64_t *packed, SpaceArgs sa, int64_t *out_raw,
-                   float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st);
 void launch_narrow_pack(const uint64_t *packed, int64_t n, const PrepArgs &layout,
                         uint32_t *narrow, cudaStream_t st);
-void launch_score_narrow(const uint32_t *narrow, const uint32_t *evaluated, int64_t N,
-                         const uint8_t *pack, const int *n_active, int D, float *s,
-                         float2 *minmax, int grid, cudaStream_t st);
 void launch_predict_full(const uint64_t *packed, int64_t count, const uint8_t *nodes,
                          const float *leaves, int K, int D, float *out, cudaStream_t st);
 void launch_mark(uint32_t *evaluated, int64_t ordinal, cudaStream_t st);
@@ -114,6 +189,7 @@ struct ktune_space {
   uint8_t pos[KTUNE_MAX_PARAMS] = {0}, width[KTUNE_MAX_PARAMS] = {0};
   uint32_t *d_narrow = nullptr;      // TS in the narrow layout (materialised, narrow spaces)
   int64_t *d_tile_offset = nullptr;  // exclusive valid prefix per raw tile (+ total)
+  std::vector<int64_t> tile_offset;  // host copy (on-the-fly spaces)
 };
 
 struct ktune_model {
@@ -141,6 +217,13 @@ struct ktune_search {
   int64_t last_scored = 0;
   bool timing = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // the step as a CUDA graph (captured on first use per stream / timing mode)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphNode_t prep_node = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  bool graph_timing = false;
+  bool use_graph = true;
   std::vector<int64_t> last_raw;
   std::vector<uint64_t> last_packed;
   // device buffers
@@ -149,9 +232,20 @@ struct ktune_search {
   int *d_nactive = nullptr, *d_active = nullptr;
   uint8_t *d_pack = nullptr;
   float *d_s = nullptr;
-  float2 *d_minmax = nullptr;
-  uint64_t *d_tilesum = nullptr;
-  float *d_stats = nullptr;
+  int mode = 0;                        // 0 one-word, 1 nibble, 2 on-the-fly one-word
+  ktune::SearchDev sdh{};              // host copy of the device descriptor
+  ktune::SearchDev *d_srch = nullptr;
+  ktune::StepDev *d_steps = nullptr;
+  ktune::ItemDev *d_items = nullptr;
+  int n_items = 0;
+  int *d_sub_search = nullptr;
+  int64_t n_sub = 0;
+  uint64_t *d_subsum = nullptr;
+  uint64_t *d_supsum = nullptr;
+  uint64_t *d_cand_key = nullptr;
+  int64_t *d_cand_raw = nullptr;
+  uint32_t *d_w = nullptr;
+  int *d_mm = nullptr;
   int64_t *d_out_raw = nullptr;
   float *d_out_score = nullptr;
   uint64_t *d_out_packed = nullptr;

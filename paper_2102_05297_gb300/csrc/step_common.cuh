@@ -1,0 +1,251 @@
+// Device functions shared by the step kernels: the expert system (Section
+// 3.4), node words and the one-word tree walk, and the integer weights of
+// Eq. score_normalization.
+#pragma once
+
+#include <float.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace ktune {
+namespace {
+
+// ---- float64 arithmetic without contraction (the expert system) ----------
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dadd_rn(a, -b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double clamp01(double x) { return fmin(1.0, fmax(0.0, x)); }
+
+// Eq. fp32_reaction
+__device__ __forceinline__ double reaction(double b, double r) {
+  if (b <= r) return 0.0;
+  return -ddiv(dsub(b, r), dsub(1.0, r));
+}
+
+// Bottleneck analysis (Section 3.4.1) and Delta-PC (Section 3.4.2) for one
+// measured counter vector; writes Delta per counter slot as float32.
+// Each formula is evaluated left to right as printed.  Utilisations are
+// percentages (X_U / 100), ins_util uses the Volta+ form min(1, ISSUE_U / 50),
+// bottlenecks are clamped to [0, 1] and Deltas to [-1, 1]; missing counters
+// take neutral values (see the table of defaults below).
+__device__ void expert_system(const float *cnt, const uint8_t *roles, int K, double r,
+                              double cores, float *delta32) {
+  double v[KTUNE_PC_N_ROLES];
+  bool has[KTUNE_PC_N_ROLES];
+  for (int i = 0; i < KTUNE_PC_N_ROLES; ++i) {
+    has[i] = false;
+    v[i] = 0.0;
+  }
+  // neutral values of counters absent from the layout
+  v[KTUNE_PC_SM_E] = 100.0;
+  v[KTUNE_PC_WARP_E] = 100.0;
+  v[KTUNE_PC_WARP_NP_E] = 100.0;
+  for (int k = 0; k < K; ++k) {
+    const int ro = roles[k];
+    if (ro < KTUNE_PC_INERT && !has[ro]) {
+      has[ro] = true;
+      v[ro] = (double)cnt[k];
+    }
+  }
+  double D[KTUNE_PC_N_ROLES];
+  for (int i = 0; i < KTUNE_PC_N_ROLES; ++i) D[i] = 0.0;
+  // Eqs. global-read / global-write and their L2 / shared analogues
+  auto mem = [&](int rt, int wt, int u) {
+    const double a = v[rt], b = v[wt], util = v[u];
+    double br = 0.0, bw = 0.0;
+    if (dadd(a, b) > 0.0) {
+      br = clamp01(dmul(ddiv(a, dadd(a, b)), ddiv(util, 100.0)));
+      bw = clamp01(dmul(ddiv(b, dadd(a, b)), ddiv(util, 100.0)));
+    }
+    D[rt] = -br;
+    D[wt] = -bw;
+  };
+  mem(KTUNE_PC_DRAM_RT, KTUNE_PC_DRAM_WT, KTUNE_PC_DRAM_U);
+  mem(KTUNE_PC_L2_RT, KTUNE_PC_L2_WT, KTUNE_PC_L2_U);
+  mem(KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT, KTUNE_PC_SHR_U);
+  D[KTUNE_PC_TEX_RWT] = -clamp01(ddiv(v[KTUNE_PC_TEX_U], 100.0));
+  // Eq. local
+  const double umax = fmax(fmax(ddiv(v[KTUNE_PC_DRAM_U], 100.0), ddiv(v[KTUNE_PC_L2_U], 100.0)),
+                           ddiv(v[KTUNE_PC_TEX_U], 100.0));
+  D[KTUNE_PC_LOC_O] = -clamp01(dmul(ddiv(v[KTUNE_PC_LOC_O], 100.0), umax));
+  // Eq. inst_fitted
+  double we = v[KTUNE_PC_WARP_E], wn = v[KTUNE_PC_WARP_NP_E];
+  if (we == 0.0) we = 100.0;
+  if (wn == 0.0) wn = 100.0;
+  const double ins_fitted =
+      dmul(dmul(dmul(32.0, v[KTUNE_PC_INST_EXE]), ddiv(100.0, we)), ddiv(100.0, wn));
+  const double issue_u = v[KTUNE_PC_INST_ISSUE_U];
+  const double ins_util = fmin(1.0, ddiv(issue_u, 50.0));
+  // Eq. fp32 and its analogues, Eq. maxutil
+  const int cls[7] = {KTUNE_PC_INST_F32, KTUNE_PC_INST_F64, KTUNE_PC_INST_INT, KTUNE_PC_INST_MISC,
+                      KTUNE_PC_INST_LDST, KTUNE_PC_INST_CONT, KTUNE_PC_INST_BCONV};
+  double util_max = 0.0;
+  for (int c = 0; c < 7; ++c) {
+    const double frac = ins_fitted > 0.0 ? ddiv(v[cls[c]], ins_fitted) : 0.0;
+    util_max = c == 0 ? frac : fmax(util_max, frac);
+    D[cls[c]] = reaction(clamp01(dmul(frac, ins_util)), r);
+  }
+  // Eq. issue
+  const double b_issue = clamp01(dmul(util_max, ddiv(dsub(100.0, issue_u), 100.0)));
+  D[KTUNE_PC_INST_ISSUE_U] = reaction(b_issue, r);
+  // parallelism, Eq. paral
+  D[KTUNE_PC_SM_E] = clamp01(ddiv(dsub(100.0, v[KTUNE_PC_SM_E]), 100.0));
+  if (has[KTUNE_PC_GLOBAL]) {
+    const double c5 = dmul(cores, 5.0);
+    D[KTUNE_PC_GLOBAL] = clamp01(fmax(0.0, ddiv(dsub(c5, v[KTUNE_PC_GLOBAL]), c5)));
+  }
+  bool seen[KTUNE_PC_N_ROLES];
+  for (int i = 0; i < KTUNE_PC_N_ROLES; ++i) seen[i] = false;
+  for (int k = 0; k < K; ++k) {
+    const int ro = roles[k];
+    float d = 0.0f;
+    if (ro < KTUNE_PC_INERT && !seen[ro]) {
+      seen[ro] = true;
+      d = (float)fmin(1.0, fmax(-1.0, D[ro]));
+    }
+    delta32[k] = d;
+  }
+}
+
+// Node word of the narrow walk for node byte (feature f, threshold t):
+// low 5 bits = s, the left shift that brings digit f to the top of the word;
+// top byte = 255 - T8 with T8 = ((t + 1) << (8 - w)) - 1, or 0 when the
+// configuration can never go right (t >= radix - 1, pass-through nodes).
+// For x = W << s the carry out of x + word is set exactly when the digit
+// exceeds t: the top byte of x is the digit followed by 8 - w bits of the
+// next digits (< 2^(8-w)), and s only fills low bits of x that are zero.
+__device__ __forceinline__ uint32_t narrow_word(uint32_t nb, const PrepArgs &pa) {
+  const int f = nb >> 4, t = nb & 15;
+  const int w = pa.width[f];
+  const uint32_t s = 32u - pa.pos[f] - w;
+  uint32_t c8 = 0;
+  if (t < pa.radix[f] - 1) c8 = 255u - ((((uint32_t)t + 1u) << (8 - w)) - 1u);
+  return (c8 << 24) | s;
+}
+
+// The same expert system run by one full warp: lane r gathers the counter of
+// role r, then lane r computes Delta of role r (the instruction lanes share
+// their fractions through shuffles for Eq. maxutil), then lane k writes the
+// float32 Delta of counter slot k.  Every formula has the operation order of
+// expert_system, so the results are bit-identical to it.
+__device__ void expert_system_warp(const float *cnt, const uint8_t *roles, int K, double r,
+                                   double cores, float *delta32, double *vals) {
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  // gather: first slot holding role `lane`
+  double v = 0.0;
+  bool has = false;
+  if (lane < KTUNE_PC_INERT) {
+    for (int k = 0; k < K; ++k)
+      if (roles[k] == lane) {
+        v = (double)cnt[k];
+        has = true;
+        break;
+      }
+    if (!has && (lane == KTUNE_PC_SM_E || lane == KTUNE_PC_WARP_E || lane == KTUNE_PC_WARP_NP_E))
+      v = 100.0;
+    vals[lane] = v;
+  }
+  const unsigned has_mask = __ballot_sync(FULL, has);
+  __syncwarp();
+  const double *V = vals;
+  double we = V[KTUNE_PC_WARP_E], wn = V[KTUNE_PC_WARP_NP_E];
+  if (we == 0.0) we = 100.0;
+  if (wn == 0.0) wn = 100.0;
+  const double ins_fitted =
+      dmul(dmul(dmul(32.0, V[KTUNE_PC_INST_EXE]), ddiv(100.0, we)), ddiv(100.0, wn));
+  const double issue_u = V[KTUNE_PC_INST_ISSUE_U];
+  const double ins_util = fmin(1.0, ddiv(issue_u, 50.0));
+  const bool is_inst = lane >= KTUNE_PC_INST_F32 && lane <= KTUNE_PC_INST_BCONV;
+  const double frac = (is_inst && ins_fitted > 0.0) ? ddiv(V[lane], ins_fitted) : 0.0;
+  // Eq. maxutil over the seven instruction classes (lanes 8..14)
+  double um = is_inst ? frac : -INFINITY;
+  for (int o = 16; o; o >>= 1) um = fmax(um, __shfl_xor_sync(FULL, um, o));
+  double D = 0.0;
+  auto mem = [&](int rt, int wt, int u, bool read) {
+    const double a = V[rt], b = V[wt], util = V[u];
+    double bb = 0.0;
+    if (dadd(a, b) > 0.0) bb = clamp01(dmul(ddiv(read ? a : b, dadd(a, b)), ddiv(util, 100.0)));
+    return -bb;
+  };
+  switch (lane) {
+    case KTUNE_PC_DRAM_RT: D = mem(KTUNE_PC_DRAM_RT, KTUNE_PC_DRAM_WT, KTUNE_PC_DRAM_U, true); break;
+    case KTUNE_PC_DRAM_WT: D = mem(KTUNE_PC_DRAM_RT, KTUNE_PC_DRAM_WT, KTUNE_PC_DRAM_U, false); break;
+    case KTUNE_PC_L2_RT: D = mem(KTUNE_PC_L2_RT, KTUNE_PC_L2_WT, KTUNE_PC_L2_U, true); break;
+    case KTUNE_PC_L2_WT: D = mem(KTUNE_PC_L2_RT, KTUNE_PC_L2_WT, KTUNE_PC_L2_U, false); break;
+    case KTUNE_PC_SHR_LT: D = mem(KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT, KTUNE_PC_SHR_U, true); break;
+    case KTUNE_PC_SHR_WT: D = mem(KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT, KTUNE_PC_SHR_U, false); break;
+    case KTUNE_PC_TEX_RWT: D = -clamp01(ddiv(V[KTUNE_PC_TEX_U], 100.0)); break;
+    case KTUNE_PC_LOC_O: {
+      const double umax = fmax(fmax(ddiv(V[KTUNE_PC_DRAM_U], 100.0), ddiv(V[KTUNE_PC_L2_U], 100.0)),
+                               ddiv(V[KTUNE_PC_TEX_U], 100.0));
+      D = -clamp01(dmul(ddiv(V[KTUNE_PC_LOC_O], 100.0), umax));
+      break;
+    }
+    case KTUNE_PC_INST_ISSUE_U:
+      D = reaction(clamp01(dmul(um, ddiv(dsub(100.0, issue_u), 100.0))), r);
+      break;
+    case KTUNE_PC_SM_E: D = clamp01(ddiv(dsub(100.0, V[KTUNE_PC_SM_E]), 100.0)); break;
+    case KTUNE_PC_GLOBAL:
+      if ((has_mask >> KTUNE_PC_GLOBAL) & 1u) {
+        const double c5 = dmul(cores, 5.0);
+        D = clamp01(fmax(0.0, ddiv(dsub(c5, V[KTUNE_PC_GLOBAL]), c5)));
+      }
+      break;
+    default:
+      if (is_inst) D = reaction(clamp01(dmul(frac, ins_util)), r);
+  }
+  __syncwarp();
+  if (lane < KTUNE_PC_INERT) vals[lane] = fmin(1.0, fmax(-1.0, D));
+  __syncwarp();
+  for (int k = lane; k < K; k += 32) {
+    const int ro = roles[k];
+    bool first = ro < KTUNE_PC_INERT;
+    for (int j = 0; j < k && first; ++j) first = roles[j] != ro;
+    delta32[k] = first ? (float)vals[ro] : 0.0f;
+  }
+  __syncwarp();
+}
+
+// ---- narrow score path (all digits in one 32-bit word) --------------------
+// One node visit: x = W << s (funnel shift by the word's low 5 bits), the
+// carry of x + word is "digit > threshold", and j = 2 j + carry moves to the
+// child in the 1-based heap.  Trees are staged group by group; a CTA runs its
+// whole range through one group before staging the next, keeping the partial
+// score in s_out between groups (same float32 value, same summation order).
+__device__ __forceinline__ uint32_t narrow_visit(uint32_t j, uint32_t word, uint32_t W) {
+  const uint32_t x = __funnelshift_l(0u, W, word);
+  uint32_t sum;
+  asm("add.cc.u32 %0, %2, %3;\n\tmadc.lo.u32 %1, %1, 2, 0;" : "=r"(sum), "+r"(j) : "r"(x), "r"(word));
+  return j;
+}
+
+// ---- normalisation and weights ---------------------------------------------
+// Eq. score_normalization in float32, each operation rounded, x^8 as
+// ((x^2)^2)^2, s = 0 mapped to 1; weight = round-half-even(s_norm * 2^20).
+__device__ __forceinline__ uint64_t weight_of(float s, float smin, float smax, float gamma) {
+  float sn;
+  if (s > 0.0f) {
+    const float x = __fadd_rn(1.0f, __fdiv_rn(s, smax));
+    const float x2 = __fmul_rn(x, x), x4 = __fmul_rn(x2, x2);
+    sn = __fmul_rn(x4, x4);
+  } else if (s > gamma) {
+    if (s == 0.0f) {
+      sn = 1.0f;
+    } else {
+      const float y = __fsub_rn(1.0f, __fdiv_rn(s, smin));
+      const float y2 = __fmul_rn(y, y), y4 = __fmul_rn(y2, y2);
+      sn = fmaxf(1e-4f, __fmul_rn(y4, y4));
+    }
+  } else {
+    sn = 1e-4f;
+  }
+  // s_norm * 2^20 <= 2^28: the 32-bit conversion (round half even) is exact
+  // and avoids the 64-bit one, which runs on the FP64 pipe
+  return (uint64_t)__float2uint_rn(__fmul_rn(sn, 1048576.0f));
+}
+
+}  // namespace
+}  // namespace ktune

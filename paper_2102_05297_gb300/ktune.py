@@ -65,7 +65,7 @@ _SIGS = {
     "ktune_search_current": ([_vp, _i64p], C.c_int),
     "ktune_search_set_profile": ([_vp, C.c_int64], C.c_int),
     "ktune_step": ([_vp, _f32p, C.c_int, _i64p, _f32p, _i32p], C.c_int),
-    "ktune_step_device": ([_vp, _vp, C.c_int, _vp, _vp, _vp, _vp], C.c_int),
+    "ktune_step_device": ([_vp, _f32p, C.c_int, _vp, _vp, _vp, _vp], C.c_int),
     "ktune_report": ([_vp, C.POINTER(C.c_double), C.c_int], C.c_int),
     "ktune_search_evaluated": ([_vp, _i64p], C.c_int),
     "ktune_search_stats": ([_vp, C.POINTER(ktune_step_stats)], C.c_int),
@@ -239,9 +239,11 @@ class Search:
             check(rc, "ktune_step")
         return self._raw[:n.value].copy(), self._score[:n.value].copy()
 
-    def step_device(self, counters_ptr: int, k: int, out_raw_ptr: int, out_score_ptr: int,
+    def step_device(self, counters, k: int, out_raw_ptr: int, out_score_ptr: int,
                     n_out_ptr: int = 0, stream=None):
-        check(lib.ktune_step_device(self.h, counters_ptr, k, out_raw_ptr, out_score_ptr,
+        """Enqueue a step; counters on the host, outputs in device memory."""
+        c, cp = _arr(counters, np.float32)
+        check(lib.ktune_step_device(self.h, cp, k, out_raw_ptr, out_score_ptr,
                                     n_out_ptr or None, _stream_ptr(stream)), "ktune_step_device")
 
     def report(self, runtimes):

@@ -262,3 +262,109 @@ def test_steps_wide_space_general_path(kt):
     gpu, cnt, rt = _synthetic(d, roles, 5)
     out = run_pair(d, model, cnt, steps=4, k=5, seed=3, runtime_fn=rt, kt=kt)
     _check(out)
+
+
+# ---- top-k select and on-the-fly spaces -------------------------------------------
+@pytest.mark.parametrize("name,K,depth,k", [("tiny", 16, 8, 5), ("batch_2", 32, 10, 16),
+                                            ("batch_7", 40, 12, 64)])
+def test_steps_topk(kt, name, K, depth, k):
+    d = W.space_tiny_block_tile() if name == "tiny" else W.load_space(name)
+    roles = W.layout(K)
+    model = random_model(d.radices, roles, depth=depth, seed=k)
+    gpu, cnt, rt = _synthetic(d, roles, 6)
+    out = run_pair(d, model, cnt, steps=6, k=k, seed=5, select="topk", runtime_fn=rt, kt=kt)
+    _check(out)
+
+
+@pytest.mark.parametrize("name,select,k", [("tiny", "sample", 5), ("batch_3", "sample", 7),
+                                           ("batch_5", "topk", 16), ("batch_0", "topk", 5)])
+def test_steps_on_the_fly(kt, name, select, k):
+    d = W.space_tiny_block_tile() if name == "tiny" else W.load_space(name)
+    roles = W.layout(32)
+    model = random_model(d.radices, roles, depth=11, seed=7)
+    gpu, cnt, rt = _synthetic(d, roles, 7)
+    out = run_pair(d, model, cnt, steps=5, k=k, seed=9, select=select, runtime_fn=rt, kt=kt,
+                   flags=kt.KTUNE_ON_THE_FLY)
+    _check(out)
+
+
+def test_on_the_fly_matches_materialised(kt):
+    d = W.load_space("batch_6")
+    roles = W.layout(16)
+    model = random_model(d.radices, roles, depth=9, seed=2)
+    outs = []
+    for flags in (kt.KTUNE_MATERIALISE, kt.KTUNE_ON_THE_FLY):
+        sp = kt.Space.from_desc(d, flags=flags)
+        m = kt.Model(sp, model)
+        s = kt.Search(sp, m, k=8, seed=3)
+        gpu, cnt, rt = _synthetic(d, roles, 1)
+        seq = []
+        for _ in range(4):
+            raw, sc = s.step(cnt(s.current()))
+            seq.append((list(raw), list(sc)))
+            s.report(rt(raw))
+        outs.append(seq)
+    assert outs[0] == outs[1]
+
+
+def test_large_on_the_fly_top16_full_size(kt):
+    """The large space at full size (113M raw, 19.5M valid, decoded every
+    step), K=40 depth-12 trees, top-16.  The oracle checks each selected
+    configuration's score exactly, validity, and that no configuration of a
+    200k random sample of the space scores higher than the 16th pick."""
+    d = W.load_space("large_16p")
+    roles = W.layout(40)
+    model = random_model(d.radices, roles, depth=12, seed=40)
+    gpu, cnt, rt = _synthetic(d, roles, 0)
+    sp = kt.Space.from_desc(d, flags=kt.KTUNE_ON_THE_FLY)
+    assert sp.count() == (counts()["large_16p"]["n_valid"], d.n_raw)
+    m = kt.Model(sp, model)
+    s = kt.Search(sp, m, k=16, seed=0, select=kt.KTUNE_SELECT_TOPK)
+    rng = np.random.default_rng(0)
+    sample = np.unique(rng.integers(0, d.n_raw, size=600000))
+    sample = sample[ospace.is_valid_raw(d, sample)][:200000]
+    seen = {s.current()}
+    for _ in range(2):
+        cp = s.current()
+        c = cnt(cp)
+        raw, sc = s.step(c)
+        assert len(raw) == 16 and len(set(raw)) == 16 and not (set(raw) & seen)
+        assert ospace.is_valid_raw(d, raw).all()
+        assert list(sc) == sorted(sc, reverse=True)
+        d32 = expert.delta_vector(roles, c).astype(np.float32)
+        prof = otrees.predict(model, ospace.decode(d.radices, [cp]))[0]
+        ref = oscore.score_fp32(prof, otrees.predict(model, ospace.decode(d.radices, raw)), d32)
+        np.testing.assert_array_equal(sc, ref)
+        free = np.array([r not in seen and r not in set(raw) for r in sample])
+        ss = oscore.score_fp32(prof, otrees.predict(model, ospace.decode(d.radices, sample[free])), d32)
+        assert ss.max() <= sc[-1]
+        seen |= set(int(r) for r in raw)
+        s.report(rt(raw))
+
+
+@pytest.mark.parametrize("select", ["sample", "topk"])
+def test_graph_path_matches_plain_launches(kt, select):
+    """Steps on a non-default stream run as a captured CUDA graph whose step
+    parameters are replaced each step; they must equal plain launches."""
+    import torch
+    d = W.load_space("batch_4")
+    roles = W.layout(32)
+    model = random_model(d.radices, roles, depth=10, seed=8)
+    gpu, cnt, rt = _synthetic(d, roles, 2)
+    sel = kt.KTUNE_SELECT_TOPK if select == "topk" else kt.KTUNE_SELECT_SAMPLE
+    runs = []
+    for stream in (None, torch.cuda.Stream()):
+        sp = kt.Space.from_desc(d)
+        m = kt.Model(sp, model)
+        s = kt.Search(sp, m, k=6, seed=4, select=sel, stream=stream)
+        seq = []
+        for i in range(6):
+            if i == 3:
+                s.set_timing(True)           # re-captures with event nodes
+            raw, sc = s.step(cnt(s.current()))
+            seq.append((list(raw), list(sc)))
+            s.report(rt(raw))
+        st = s.stats()
+        assert st.n_kernels == 4 and st.kernel_ms[1] > 0
+        runs.append(seq)
+    assert runs[0] == runs[1]
