@@ -237,6 +237,35 @@ int ktune_search_stats(ktune_search *search, ktune_step_stats *out);
 /* Enable (1) or disable (0) per-kernel event timing of later steps. */
 int ktune_search_set_timing(ktune_search *search, int enable);
 
+/* ---- batched steps (many searches per launch) -------------------------------
+ * A batch groups up to 64 searches (over any spaces and models) that share the
+ * space mode (materialised one-word digits, materialised two-word digits, or
+ * on-the-fly) and the select mode.  One ktune_batch_step runs one step of every
+ * search with a single launch of each step kernel (on a non-default stream: one
+ * CUDA graph launch); work items are ranges of the searches' spaces balanced
+ * over the SMs.  Each search keeps its own state: continue with ktune_report
+ * on the member handles.  The searches must outlive the batch. */
+typedef struct ktune_batch ktune_batch;
+int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune_batch **out);
+int ktune_batch_destroy(ktune_batch *batch);
+/* counters: n HOST arrays, counters[i] holding search i's K_i measured
+ * counters.  Outputs (HOST): out_raw[i * k + j], out_score[i * k + j] for the
+ * j-th configuration selected for search i, n_out[i] of them.  Returns
+ * KTUNE_EXHAUSTED if any search ran out (its n_out[i] < k). */
+int ktune_batch_step(ktune_batch *batch, const float *const *counters, int k, int64_t *out_raw,
+                     float *out_score, int *n_out);
+/* The project's autotuner: times the scoring kernels (which leave the
+ * searches' states untouched) for each candidate CTA shape, configurations per
+ * thread and work-item granularity on this batch, with these counters, `reps`
+ * times each, and keeps the fastest for later steps.  *choice receives its
+ * index; ms_out (may be NULL) receives the mean milliseconds of each candidate
+ * in the order of ktune_batch_variant. */
+int ktune_batch_autotune(ktune_batch *batch, const float *const *counters, int reps, int *choice,
+                         float *ms_out, int n_ms);
+/* Candidate v of the autotuner: CTA threads, configurations per thread, work
+ * items per CTA.  Returns the number of candidates. */
+int ktune_batch_variant(int v, int *threads, int *cpt, int *items_per_cta);
+
 /* ---- scoring without device allocation ------------------------------------
  * No counterpart in the paper: this is a deployment convenience.
  *

@@ -1009,3 +1009,298 @@ int ktune_report(ktune_search *h, const double *runtimes, int n) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched steps
+namespace {
+
+struct BatchVariant {
+  int score_variant, items_per_cta;
+};
+const BatchVariant kBatchVariants[] = {{0, 1}, {0, 4}, {1, 1}, {2, 1}, {2, 4}, {3, 1}, {4, 1}, {4, 4}};
+constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
+
+// Work items of the batch: every search's space (ordinals, or raw tiles when on
+// the fly) cut into pieces of about total / (SMs * items_per_cta) units.
+int batch_items(ktune_batch *b) {
+  std::vector<ItemDev> items;
+  int64_t total = 0;
+  for (ktune_search *h : b->s) total += b->mode == 2 ? h->space->n_tiles : h->space->n_valid;
+  const int64_t target =
+      std::max<int64_t>(b->mode == 2 ? 1 : 1024, total / ((int64_t)b->num_sms * b->items_per_cta));
+  for (size_t i = 0; i < b->s.size(); ++i) {
+    ktune_search *h = b->s[i];
+    const int64_t units = b->mode == 2 ? h->space->n_tiles : h->space->n_valid;
+    const int64_t pieces = std::max<int64_t>(1, (units + target - 1) / target);
+    b->sdh[i].item_begin = (int64_t)items.size();
+    for (int64_t q = 0; q < pieces; ++q) {
+      ItemDev it{};
+      it.search = (int)i;
+      it.lo = units * q / pieces;
+      it.hi = units * (q + 1) / pieces;
+      if (it.hi > it.lo) items.push_back(it);
+    }
+    b->sdh[i].item_end = (int64_t)items.size();
+  }
+  b->n_items = (int)items.size();
+  b->grid = std::min<int>(b->n_items, b->num_sms);
+  cudaFree(b->d_items);
+  cudaFree(b->d_cand_key);
+  cudaFree(b->d_cand_raw);
+  b->d_items = nullptr;
+  b->d_cand_key = nullptr;
+  b->d_cand_raw = nullptr;
+  int rc;
+  if ((rc = dalloc(&b->d_items, items.size())) ||
+      (rc = dalloc(&b->d_cand_key, items.size() * KTUNE_MAX_K)) ||
+      (rc = dalloc(&b->d_cand_raw, items.size() * KTUNE_MAX_K)))
+    return rc;
+  for (size_t i = 0; i < b->s.size(); ++i) {
+    // candidates of search i live after those of the searches before it; the
+    // kernels index them by (item - item_begin)
+    b->sdh[i].cand_key = b->d_cand_key + b->sdh[i].item_begin * KTUNE_MAX_K;
+    b->sdh[i].cand_raw = b->d_cand_raw + b->sdh[i].item_begin * KTUNE_MAX_K;
+  }
+  CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(ItemDev),
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_srch, b->sdh.data(), b->sdh.size() * sizeof(SearchDev),
+                     cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  return KTUNE_OK;
+}
+
+void batch_drop_graph(ktune_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->prep_node = nullptr;
+}
+
+int batch_fill_steps(ktune_batch *b, const float *const *counters, int k, StepBatch<kMaxBatch> &sb) {
+  for (size_t i = 0; i < b->s.size(); ++i) {
+    ktune_search *h = b->s[i];
+    const int K = h->model->K;
+    if (!counters[i]) FAIL(KTUNE_EINVAL, "null counters");
+    for (int q = 0; q < K; ++q)
+      if (!isfinite(counters[i][q])) FAIL(KTUNE_EINVAL, "non-finite profiled counter");
+    StepDev &sp = sb.st[i];
+    sp.cprof_packed = h->cprof_packed;
+    host_expert(h->model->roles.data(), K, counters[i], h->opts.inst_reaction, h->opts.cores,
+                sp.delta);
+    sp.out_raw = b->d_out_raw + i * KTUNE_MAX_K;
+    sp.out_score = b->d_out_score + i * KTUNE_MAX_K;
+    sp.out_packed = b->d_out_packed + i * KTUNE_MAX_K;
+    sp.n_out = b->d_nout + i;
+    sp.step = h->step_no;
+    sp.k = k;
+  }
+  return KTUNE_OK;
+}
+
+void batch_launch(ktune_batch *b, const StepBatch<kMaxBatch> &sb, cudaStream_t st, bool score_only) {
+  const int S = (int)b->s.size();
+  launch_bprep<kMaxBatch>(b->d_srch, b->d_steps, sb, S, b->K_max, b->D_max, st);
+  launch_bscore(b->d_srch, b->d_steps, b->d_items, b->n_items, b->mode, b->topk, b->grid, st,
+                b->variant);
+  if (score_only) return;
+  if (!b->topk) launch_bweights(b->d_srch, b->d_sub_search, b->n_sub, st);
+  launch_bselect(b->d_srch, b->d_steps, S, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ktune_batch_variant(int v, int *threads, int *cpt, int *items_per_cta) {
+  if (v >= 0 && v < kNumBatchVariants) {
+    if (threads) *threads = bscore_variant_threads(kBatchVariants[v].score_variant);
+    if (cpt) *cpt = bscore_variant_cpt(kBatchVariants[v].score_variant);
+    if (items_per_cta) *items_per_cta = kBatchVariants[v].items_per_cta;
+  }
+  return kNumBatchVariants;
+}
+
+int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune_batch **out) {
+  if (!searches || !out || n < 1) FAIL(KTUNE_EINVAL, "null argument or empty batch");
+  if (n > kMaxBatch) FAIL(KTUNE_EINVAL, "more than 64 searches in a batch");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!searches[i]) FAIL(KTUNE_EINVAL, "null search");
+    if (searches[i]->mode != searches[0]->mode || searches[i]->opts.select != searches[0]->opts.select)
+      FAIL(KTUNE_EINVAL, "searches of a batch must share the space mode and the select mode");
+  }
+  ktune_batch *b = new (std::nothrow) ktune_batch();
+  if (!b) FAIL(KTUNE_ENOMEM, "host allocation");
+  auto fail = [&](int rc) {
+    ktune_batch_destroy(b);
+    return rc;
+  };
+  b->s.assign(searches, searches + n);
+  b->mode = searches[0]->mode;
+  b->topk = searches[0]->opts.select == KTUNE_SELECT_TOPK;
+  b->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<int> sub_search;
+  for (int i = 0; i < n; ++i) {
+    ktune_search *h = searches[i];
+    b->K_max = std::max(b->K_max, h->model->K);
+    b->D_max = std::max(b->D_max, h->model->D);
+    SearchDev sd = h->sdh;
+    sd.sub_begin = (int64_t)sub_search.size();
+    for (int64_t g = 0; g < h->n_sub; ++g) sub_search.push_back(i);
+    b->sdh.push_back(sd);
+  }
+  b->n_sub = (int64_t)sub_search.size();
+  int rc;
+  if ((rc = dalloc(&b->d_srch, n)) || (rc = dalloc(&b->d_steps, n)) ||
+      (rc = dalloc(&b->d_sub_search, sub_search.size())) ||
+      (rc = dalloc(&b->d_out_raw, (size_t)n * KTUNE_MAX_K)) ||
+      (rc = dalloc(&b->d_out_score, (size_t)n * KTUNE_MAX_K)) ||
+      (rc = dalloc(&b->d_out_packed, (size_t)n * KTUNE_MAX_K)) || (rc = dalloc(&b->d_nout, n)))
+    return fail(rc);
+  if (cudaMallocHost((void **)&b->h_out_raw, (size_t)n * KTUNE_MAX_K * 8) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_out_score, (size_t)n * KTUNE_MAX_K * 4) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_out_packed, (size_t)n * KTUNE_MAX_K * 8) != cudaSuccess ||
+      cudaMallocHost((void **)&b->h_nout, (size_t)n * 4) != cudaSuccess) {
+    set_error("pinned host allocation failed");
+    return fail(KTUNE_ENOMEM);
+  }
+  if (cudaMemcpyAsync(b->d_sub_search, sub_search.data(), sub_search.size() * 4,
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+    set_error("upload failed");
+    return fail(KTUNE_ECUDA);
+  }
+  if ((rc = batch_items(b))) return fail(rc);
+  *out = b;
+  return KTUNE_OK;
+}
+
+int ktune_batch_destroy(ktune_batch *b) {
+  if (!b) return KTUNE_OK;
+  void *dev[] = {b->d_srch, b->d_steps, b->d_items, b->d_sub_search, b->d_cand_key, b->d_cand_raw,
+                 b->d_out_raw, b->d_out_score, b->d_out_packed, b->d_nout};
+  for (void *p : dev) cudaFree(p);
+  void *pin[] = {b->h_out_raw, b->h_out_score, b->h_out_packed, b->h_nout};
+  for (void *p : pin) cudaFreeHost(p);
+  batch_drop_graph(b);
+  delete b;
+  return KTUNE_OK;
+}
+
+int ktune_batch_step(ktune_batch *b, const float *const *counters, int k, int64_t *out_raw,
+                     float *out_score, int *n_out) {
+  if (!b || !counters || !out_raw || !out_score || !n_out) FAIL(KTUNE_EINVAL, "null argument");
+  if (k < 1 || k > KTUNE_MAX_K) FAIL(KTUNE_EINVAL, "k out of range");
+  static thread_local StepBatch<kMaxBatch> sb;
+  memset(&sb, 0, sizeof(sb));
+  TRY(batch_fill_steps(b, counters, k, sb));
+  const int S = (int)b->s.size();
+  cudaStream_t st = b->stream;
+  if (st) {
+    if (b->gexec && b->graph_stream != st) batch_drop_graph(b);
+    if (!b->gexec) {
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      batch_launch(b, sb, st, false);
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamEndCapture(st, &g));
+      b->graph = g;
+      size_t nn = 0;
+      CK(cudaGraphGetNodes(g, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        CK(cudaGraphKernelNodeGetParams(nd, &kp));
+        if (kp.func == bprep_func<kMaxBatch>()) b->prep_node = nd;
+      }
+      if (!b->prep_node) FAIL(KTUNE_ECUDA, "graph capture lost the prepare kernel");
+      CK(cudaGraphInstantiate(&b->gexec, g, 0));
+      b->graph_stream = st;
+    } else {
+      cudaKernelNodeParams kp{};
+      CK(cudaGraphKernelNodeGetParams(b->prep_node, &kp));
+      void *args[] = {&b->d_srch, &b->d_steps, &sb};
+      kp.kernelParams = args;
+      kp.extra = nullptr;
+      CK(cudaGraphExecKernelNodeSetParams(b->gexec, b->prep_node, &kp));
+    }
+    CK(cudaGraphLaunch(b->gexec, st));
+  } else {
+    batch_launch(b, sb, st, false);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(b->h_out_raw, b->d_out_raw, (size_t)S * KTUNE_MAX_K * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(b->h_out_score, b->d_out_score, (size_t)S * KTUNE_MAX_K * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(b->h_out_packed, b->d_out_packed, (size_t)S * KTUNE_MAX_K * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(b->h_nout, b->d_nout, (size_t)S * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  bool exhausted = false;
+  for (int i = 0; i < S; ++i) {
+    ktune_search *h = b->s[i];
+    const int no = b->h_nout[i];
+    n_out[i] = no;
+    exhausted |= no < k;
+    for (int j = 0; j < no; ++j) {
+      out_raw[(size_t)i * k + j] = b->h_out_raw[(size_t)i * KTUNE_MAX_K + j];
+      out_score[(size_t)i * k + j] = b->h_out_score[(size_t)i * KTUNE_MAX_K + j];
+    }
+    h->last_raw.assign(b->h_out_raw + (size_t)i * KTUNE_MAX_K, b->h_out_raw + (size_t)i * KTUNE_MAX_K + no);
+    h->last_packed.assign(b->h_out_packed + (size_t)i * KTUNE_MAX_K,
+                          b->h_out_packed + (size_t)i * KTUNE_MAX_K + no);
+    h->last_scored = h->space->n_valid - h->n_evaluated;
+    h->n_evaluated += no;
+    h->step_no++;
+    h->last_stream = st;
+  }
+  if (exhausted) FAIL(KTUNE_EXHAUSTED, "a search has fewer unevaluated configurations than requested");
+  return KTUNE_OK;
+}
+
+int ktune_batch_autotune(ktune_batch *b, const float *const *counters, int reps, int *choice,
+                         float *ms_out, int n_ms) {
+  if (!b || !counters || reps < 1) FAIL(KTUNE_EINVAL, "bad argument");
+  static thread_local StepBatch<kMaxBatch> sb;
+  memset(&sb, 0, sizeof(sb));
+  TRY(batch_fill_steps(b, counters, 1, sb));
+  cudaStream_t st = b->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = INFINITY;
+  const int nv = b->mode == 2 ? 1 : kNumBatchVariants;   // on-the-fly spaces have one shape
+  for (int v = 0; v < nv; ++v) {
+    b->variant = kBatchVariants[v].score_variant;
+    b->items_per_cta = kBatchVariants[v].items_per_cta;
+    TRY(batch_items(b));
+    batch_launch(b, sb, st, true);   // warm-up (scoring only: no search state changes)
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) batch_launch(b, sb, st, true);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= reps;
+    if (ms_out && v < n_ms) ms_out[v] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = kBatchVariants[best].score_variant;
+  b->items_per_cta = kBatchVariants[best].items_per_cta;
+  TRY(batch_items(b));
+  batch_drop_graph(b);
+  if (choice) *choice = best;
+  return KTUNE_OK;
+}
+
+}  // extern "C"

@@ -137,9 +137,11 @@ const void *bprep_func();
 // the operation order of the equations; Delta per counter slot as float32.
 void host_expert(const int *roles, int K, const float *counters, double inst_reaction,
                  double cores, float *delta32);
-int bscore_threads();
+int bscore_variants();
+int bscore_variant_threads(int v);
+int bscore_variant_cpt(int v);
 void launch_bscore(const SearchDev *srch, const StepDev *steps, const ItemDev *items, int n_items,
-                   int mode, bool topk, int grid, cudaStream_t st);
+                   int mode, bool topk, int grid, cudaStream_t st, int variant = 0);
 void launch_bweights(const SearchDev *srch, const int *sub_search, int64_t n_sub_total,
                      cudaStream_t st);
 void launch_bselect(const SearchDev *srch, const StepDev *steps, int S, cudaStream_t st);
@@ -200,6 +202,37 @@ struct ktune_model {
   std::vector<int> roles;
   uint8_t *d_nodes = nullptr;   // [K][2^D] node bytes (feature << 4 | threshold)
   float *d_leaves = nullptr;    // [K][2^D]
+};
+
+struct ktune_batch {
+  std::vector<ktune_search *> s;
+  int mode = 0;
+  bool topk = false;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int K_max = 0, D_max = 0;
+  int variant = 0, items_per_cta = 1;
+  int n_items = 0, grid = 0;
+  int64_t n_sub = 0;
+  std::vector<ktune::SearchDev> sdh;
+  ktune::SearchDev *d_srch = nullptr;
+  ktune::StepDev *d_steps = nullptr;
+  ktune::ItemDev *d_items = nullptr;
+  int *d_sub_search = nullptr;
+  uint64_t *d_cand_key = nullptr;
+  int64_t *d_cand_raw = nullptr;
+  int64_t *d_out_raw = nullptr;
+  float *d_out_score = nullptr;
+  uint64_t *d_out_packed = nullptr;
+  int *d_nout = nullptr;
+  int64_t *h_out_raw = nullptr;
+  float *h_out_score = nullptr;
+  uint64_t *h_out_packed = nullptr;
+  int *h_nout = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphNode_t prep_node = nullptr;
+  cudaStream_t graph_stream = nullptr;
 };
 
 struct ktune_search {

@@ -25,9 +25,6 @@ namespace ktune {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kBThreads = 512;
-constexpr int kBWarps = kBThreads / 32;
-constexpr int kTopkBytes = kBWarps * KTUNE_MAX_K * 16;   // per-warp lists (key + raw)
 constexpr int kOtfCap = 4096;                           // on-the-fly list capacity
 constexpr int kOtfBytes = kOtfCap * 12;                 // (W, ordinal, raw32)
 constexpr int kSelB = 256;   // select CTA size (the draws themselves run in warp 0)
@@ -179,12 +176,13 @@ __device__ __forceinline__ void topk_offer(uint64_t *key, int64_t *raw, int k, b
 }
 
 // Merge the CTA's warp lists into the item's top k (k rounds of block argmax).
+template <int NW>
 __device__ void topk_merge_cta(uint64_t *lkey, int64_t *lraw, int k, uint64_t *out_key,
                                int64_t *out_raw) {
-  __shared__ uint64_t wbest[kBWarps];
-  __shared__ int widx[kBWarps];
+  __shared__ uint64_t wbest[NW];
+  __shared__ int widx[NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n = kBWarps * KTUNE_MAX_K;
+  const int n = NW * KTUNE_MAX_K;
   __syncthreads();
   for (int r = 0; r < k; ++r) {
     uint64_t best = 0;
@@ -213,7 +211,7 @@ __device__ void topk_merge_cta(uint64_t *lkey, int64_t *lraw, int k, uint64_t *o
     if (threadIdx.x == 0) {
       uint64_t b = 0;
       int i = -1;
-      for (int w = 0; w < kBWarps; ++w)
+      for (int w = 0; w < NW; ++w)
         if (wbest[w] > b) {
           b = wbest[w];
           i = widx[w];
@@ -289,11 +287,14 @@ __device__ T block_incl(T v, T *sh, T *total) {
 }
 
 // ---- score ---------------------------------------------------------------------------
-template <int CPT, int MODE, bool TOPK>
-__global__ void __launch_bounds__(kBThreads, 1)
+template <int THREADS, int CPT, int MODE, bool TOPK>
+__global__ void __launch_bounds__(THREADS, 1)
     k_bscore(const SearchDev *__restrict__ srch, const StepDev *__restrict__ steps,
              const ItemDev *__restrict__ items, int n_items) {
   extern __shared__ __align__(16) uint8_t smem[];
+  constexpr int kBThreads = THREADS;
+  constexpr int kBWarps = THREADS / 32;
+  constexpr int kTopkBytes = kBWarps * KTUNE_MAX_K * 16;   // per-warp lists (key + raw)
   __shared__ float red_mn[kBWarps], red_mx[kBWarps];
   __shared__ uint32_t shc[32];
   __shared__ int sh_count;
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
         }
       };
 
-      if (MODE != 2) {
+      if constexpr (MODE != 2) {
         // chunk c + 1's inputs are loaded while chunk c walks
         constexpr int64_t kStep = (int64_t)kBThreads * CPT;
         uint32_t Wn[CPT];
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(kBThreads, 1)
     }
     if (topk) {
       const int64_t ci = (int64_t)(item - sd.item_begin) * KTUNE_MAX_K;
-      topk_merge_cta(reinterpret_cast<uint64_t *>(tk_base),
+      topk_merge_cta<kBWarps>(reinterpret_cast<uint64_t *>(tk_base),
                      reinterpret_cast<int64_t *>(tk_base + kBWarps * KTUNE_MAX_K * 8), k,
                      sd.cand_key + ci, sd.cand_raw + ci);
     }
@@ -950,34 +951,58 @@ const void *bprep_func() {
 template const void *bprep_func<1>();
 template const void *bprep_func<kMaxBatch>();
 
-int bscore_threads() { return kBThreads; }
+// Score-kernel variants the autotuner chooses from: (CTA threads, configurations
+// per thread).  On-the-fly spaces always use (512, 4).
+struct ScoreVariant {
+  int threads, cpt;
+};
+static const ScoreVariant kVariants[] = {{512, 8}, {512, 4}, {256, 8}, {256, 16}, {384, 8}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
+int bscore_variants() { return kNumVariants; }
+int bscore_variant_threads(int v) { return kVariants[v].threads; }
+int bscore_variant_cpt(int v) { return kVariants[v].cpt; }
 
-
-template <int MODE, bool TOPK>
-static void launch_mode(const SearchDev *srch, const StepDev *steps, const ItemDev *items,
-                        int n_items, int grid, cudaStream_t st) {
-  constexpr int CPT = MODE == 2 ? 4 : kScoreCPT;
+template <int THREADS, int CPT, int MODE, bool TOPK>
+static void launch_one(const SearchDev *srch, const StepDev *steps, const ItemDev *items,
+                       int n_items, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_bscore<CPT, MODE, TOPK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSmemBudget);
+    cudaFuncSetAttribute(k_bscore<THREADS, CPT, MODE, TOPK>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
     attr = true;
   }
-  k_bscore<CPT, MODE, TOPK><<<grid, kBThreads, kSmemBudget, st>>>(srch, steps, items, n_items);
+  k_bscore<THREADS, CPT, MODE, TOPK><<<grid, THREADS, kSmemBudget, st>>>(srch, steps, items, n_items);
+}
+
+template <int MODE, bool TOPK>
+static void launch_variant(int v, const SearchDev *srch, const StepDev *steps, const ItemDev *items,
+                           int n_items, int grid, cudaStream_t st) {
+  if constexpr (MODE == 2) {
+    launch_one<512, 4, 2, TOPK>(srch, steps, items, n_items, grid, st);
+    return;
+  } else {
+  switch (v) {
+    case 1: launch_one<512, 4, MODE, TOPK>(srch, steps, items, n_items, grid, st); break;
+    case 2: launch_one<256, 8, MODE, TOPK>(srch, steps, items, n_items, grid, st); break;
+    case 3: launch_one<256, 16, MODE, TOPK>(srch, steps, items, n_items, grid, st); break;
+    case 4: launch_one<384, 8, MODE, TOPK>(srch, steps, items, n_items, grid, st); break;
+    default: launch_one<512, 8, MODE, TOPK>(srch, steps, items, n_items, grid, st);
+  }
+  }
 }
 
 // All searches of one launch share the space mode and the select mode.
 void launch_bscore(const SearchDev *srch, const StepDev *steps, const ItemDev *items, int n_items,
-                   int mode, bool topk, int grid, cudaStream_t st) {
+                   int mode, bool topk, int grid, cudaStream_t st, int variant) {
   if (topk) {
-    if (mode == 0) launch_mode<0, true>(srch, steps, items, n_items, grid, st);
-    else if (mode == 1) launch_mode<1, true>(srch, steps, items, n_items, grid, st);
-    else launch_mode<2, true>(srch, steps, items, n_items, grid, st);
+    if (mode == 0) launch_variant<0, true>(variant, srch, steps, items, n_items, grid, st);
+    else if (mode == 1) launch_variant<1, true>(variant, srch, steps, items, n_items, grid, st);
+    else launch_variant<2, true>(variant, srch, steps, items, n_items, grid, st);
   } else {
-    if (mode == 0) launch_mode<0, false>(srch, steps, items, n_items, grid, st);
-    else if (mode == 1) launch_mode<1, false>(srch, steps, items, n_items, grid, st);
-    else launch_mode<2, false>(srch, steps, items, n_items, grid, st);
+    if (mode == 0) launch_variant<0, false>(variant, srch, steps, items, n_items, grid, st);
+    else if (mode == 1) launch_variant<1, false>(variant, srch, steps, items, n_items, grid, st);
+    else launch_variant<2, false>(variant, srch, steps, items, n_items, grid, st);
   }
 }
 

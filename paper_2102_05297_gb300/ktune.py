@@ -70,6 +70,11 @@ _SIGS = {
     "ktune_search_evaluated": ([_vp, _i64p], C.c_int),
     "ktune_search_stats": ([_vp, C.POINTER(ktune_step_stats)], C.c_int),
     "ktune_search_set_timing": ([_vp, C.c_int], C.c_int),
+    "ktune_batch_create": ([C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)], C.c_int),
+    "ktune_batch_destroy": ([_vp], C.c_int),
+    "ktune_batch_step": ([_vp, C.POINTER(_f32p), C.c_int, _i64p, _f32p, _i32p], C.c_int),
+    "ktune_batch_autotune": ([_vp, C.POINTER(_f32p), C.c_int, _i32p, _f32p, C.c_int], C.c_int),
+    "ktune_batch_variant": ([C.c_int, _i32p, _i32p, _i32p], C.c_int),
     "ktune_score_noalloc": ([_vp, C.c_int64, _vp, _vp, _vp, C.c_int, C.c_int, _i32p, _vp,
                              C.c_uint64, C.c_double, C.c_double, _vp, _vp, _vp], C.c_int),
 }
@@ -266,6 +271,61 @@ class Search:
     def close(self):
         if getattr(self, "h", None):
             lib.ktune_search_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class Batch:
+    """Owns a ktune_batch over Search objects (which must outlive it)."""
+
+    def __init__(self, searches, stream=None):
+        self.searches = list(searches)
+        arr = (C.c_void_p * len(self.searches))(*[x.h.value for x in self.searches])
+        h = C.c_void_p()
+        check(lib.ktune_batch_create(arr, len(arr), _stream_ptr(stream), C.byref(h)),
+              "ktune_batch_create")
+        self.h = h
+
+    def _counters(self, counters):
+        keep = [np.ascontiguousarray(c, dtype=np.float32) for c in counters]
+        ptrs = (C.POINTER(C.c_float) * len(keep))(
+            *[c.ctypes.data_as(C.POINTER(C.c_float)) for c in keep])
+        return keep, ptrs
+
+    def step(self, counters, k: int):
+        """One step of every search; returns per search (raw indices, scores)."""
+        n = len(self.searches)
+        keep, ptrs = self._counters(counters)
+        raw = np.zeros(n * k, np.int64)
+        sc = np.zeros(n * k, np.float32)
+        no = np.zeros(n, np.int32)
+        rc = lib.ktune_batch_step(self.h, ptrs, k, raw.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  sc.ctypes.data_as(C.POINTER(C.c_float)),
+                                  no.ctypes.data_as(C.POINTER(C.c_int)))
+        if rc not in (KTUNE_OK, KTUNE_EXHAUSTED):
+            check(rc, "ktune_batch_step")
+        return [(raw[i * k:i * k + no[i]].copy(), sc[i * k:i * k + no[i]].copy()) for i in range(n)]
+
+    def autotune(self, counters, reps: int = 5):
+        keep, ptrs = self._counters(counters)
+        nv = lib.ktune_batch_variant(0, None, None, None)
+        ms = np.zeros(nv, np.float32)
+        ch = C.c_int()
+        check(lib.ktune_batch_autotune(self.h, ptrs, reps, C.byref(ch),
+                                       ms.ctypes.data_as(C.POINTER(C.c_float)), nv),
+              "ktune_batch_autotune")
+        return ch.value, ms
+
+    @staticmethod
+    def variant(v: int):
+        t, c, i = C.c_int(), C.c_int(), C.c_int()
+        lib.ktune_batch_variant(v, C.byref(t), C.byref(c), C.byref(i))
+        return t.value, c.value, i.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ktune_batch_destroy(self.h)
             self.h = None
 
     __del__ = close
