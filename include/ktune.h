@@ -266,6 +266,64 @@ int ktune_batch_autotune(ktune_batch *batch, const float *const *counters, int r
  * items per CTA.  Returns the number of candidates. */
 int ktune_batch_variant(int v, int *threads, int *cpt, int *items_per_cta);
 
+/* ---- the MLP counter model (Section 3.3's predictor, as a neural network) --
+ * Section 3.3 predicts a configuration's counters with a model built from the
+ * profiles the search collected (the paper uses regression trees); this model
+ * is a multilayer perceptron trained on the GPU:
+ *   features  per parameter the one-hot digit, then per parameter
+ *             u = 2 (log2(1 + v) - lo) / (hi - lo) - 1 over its value list
+ *             (0 for a one-valued parameter), zero-padded to F (multiple of 16)
+ *   network   z1 = x W1^T + b1, a1 = GELU(z1) (erf form); z2, a2; z3, a3 (256
+ *             wide); y = a3 W4^T + b4; counter c predicted as y_c * range_c
+ *   numerics  x, weights and a1..a3 in bfloat16 (round to nearest even),
+ *             products accumulated in float32 on the tensor cores; biases,
+ *             pre-activations and outputs float32
+ *   training  mean over rows and the K counters of (y - t / range)^2, Adam
+ *             (Kingma & Ba) on float32 master weights, beta (0.9, 0.999),
+ *             eps 1e-8; backward products take bfloat16 operands
+ * Parameters, flat float32 vector (host): W1[256][F], b1[256], W2[256][256],
+ * b2[256], W3[256][256], b3[256], W4[K][256], b4[K] (row-major). */
+typedef struct ktune_mlp ktune_mlp;
+/* roles: HOST int32[K] (KTUNE_PC_*), ranges: HOST float[K] > 0 (finite);
+ * max_batch: largest training batch, a multiple of 16 in 16..65536.
+ * Parameters start at zero and the Adam state empty.  Requires F <= 384. */
+int ktune_mlp_create(ktune_space *s, int K, const int32_t *roles, const float *ranges,
+                     int max_batch, void *stream, ktune_mlp **out);
+int ktune_mlp_destroy(ktune_mlp *m);
+/* F (feature columns) and the length of the flat parameter vector. */
+int ktune_mlp_info(const ktune_mlp *m, int *F, int64_t *n_params);
+/* Replace the parameters (HOST, flat layout above); resets Adam (zero moments,
+ * step 0).  get copies the current float32 master parameters out. */
+int ktune_mlp_set_params(ktune_mlp *m, const float *params);
+int ktune_mlp_get_params(const ktune_mlp *m, float *params);
+/* Training set: n valid configurations by raw index (HOST int64[n]) and their
+ * measured counters (HOST float[n][K]).  Replaces any previous set. */
+int ktune_mlp_set_data(ktune_mlp *m, const int64_t *raw, const float *counters, int64_t n);
+/* One forward and backward pass over training rows idx[0..B) (HOST int32,
+ * B a multiple of 16, <= max_batch) without an update: *loss gets the mean
+ * squared error, grads (HOST, flat layout, may be NULL) the gradients. */
+int ktune_mlp_grads(ktune_mlp *m, const int32_t *idx, int B, double *loss, float *grads);
+/* `steps` Adam steps with learning rate lr; step t trains on the rows
+ * idx[t * B .. t * B + B) (HOST int32[steps * B]).  losses (HOST, may be
+ * NULL) receives each step's loss before its update. */
+int ktune_mlp_train(ktune_mlp *m, const int32_t *idx, int B, int steps, float lr, double *losses);
+/* Predicted counters (HOST float[n][K]) of configurations given by raw index
+ * (HOST int64[n]; any raw index of the space). */
+int ktune_mlp_predict(ktune_mlp *m, const int64_t *raw, int64_t n, float *out);
+/* Predicted counters of TS[first .. first + count) into device float[count][K]
+ * (materialised spaces); enqueued on `stream`. */
+int ktune_mlp_predict_device(ktune_mlp *m, int64_t first, int64_t count, float *out, void *stream);
+
+/* The tensor-core GEMM the MLP trains with, exposed for validation (no
+ * counterpart in the paper): C[M][N] = A[M][Kd] * B[N][Kd]^T, all device
+ * buffers, A and B bfloat16 bit patterns (uint16) row-major with leading
+ * dimensions lda, ldb (multiples of 8, 16-byte aligned rows), C float32 with
+ * leading dimension ldc; Kd a multiple of 16; N a multiple of 16.  Enqueued
+ * on `stream`, then synchronised (the call reports a tensor-core wait that
+ * timed out as KTUNE_ETIMEOUT). */
+int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, float *C, int ldc,
+                    int M, int N, int Kd, void *stream);
+
 /* ---- scoring without device allocation ------------------------------------
  * No counterpart in the paper: this is a deployment convenience.
  *

@@ -172,6 +172,10 @@ int build_groups(ktune_space *s, const int32_t *code, int n) {
   return KTUNE_OK;
 }
 
+}  // namespace
+
+namespace ktune {
+
 uint64_t host_pack(const ktune_space *s, int64_t raw) {
   uint64_t p = 0;
   for (int j = s->sa.P - 1; j >= 0; --j) {
@@ -190,16 +194,9 @@ bool host_valid(const ktune_space *s, uint64_t p) {
   return true;
 }
 
-template <typename T>
-int dalloc(T **p, size_t n) {
-  if (n == 0) n = 1;
-  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
-  if (e != cudaSuccess) {
-    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    return KTUNE_ENOMEM;
-  }
-  return KTUNE_OK;
-}
+}  // namespace ktune
+
+namespace {
 
 #define TRY(x)          \
   do {                  \

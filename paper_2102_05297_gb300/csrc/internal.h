@@ -169,8 +169,72 @@ void launch_predict_full(const uint64_t *packed, int64_t count, const uint8_t *n
                          const float *leaves, int K, int D, float *out, cudaStream_t st);
 void launch_mark(uint32_t *evaluated, int64_t ordinal, cudaStream_t st);
 
+// ---- MLP counter model (k_mlp.cu) ----
+constexpr int kMlpHidden = 256;
+constexpr int kMlpMaxF = 384;           // feature columns (multiple of 16)
+
+// The network as the fused forward kernel reads it (all device pointers).
+struct MlpDev {
+  int P, F, K, Kp;          // parameters, feature columns, counters, counters padded to 16
+  const uint16_t *w[4];     // bf16 row-major: 256 x F, 256 x 256, 256 x 256, Kp x 256
+  const float *b[4];        // float32 biases (b[3] padded to Kp)
+  const float *range;       // [K] output scale per counter
+  const int *off;           // [P + 1] one-hot offset per parameter; off[P] = start of the u block
+  const uint16_t *utab;     // [P][16] bf16 u value per digit
+};
+
+// Epilogue operands of the training GEMM (see k_gemm_tc).
+struct EpiArgs {
+  float *c = nullptr;
+  int ldc = 0;
+  const float *bias = nullptr;
+  float *z = nullptr;
+  int ldz = 0;
+  uint16_t *a = nullptr;
+  int lda = 0;
+  uint16_t *at = nullptr;
+  int ldat = 0;
+};
+
+int mlp_fwd_smem(int F);
+void launch_gemm_tc(int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
+                    int K, const EpiArgs &ep, int *status, cudaStream_t st);
+void launch_features(const uint64_t *packed, const int *idx, int B, int P, int F, const int *off,
+                     const uint16_t *utab, uint16_t *X, cudaStream_t st);
+void launch_transpose(const uint16_t *src, int lds, uint16_t *dst, int ldd, int R, int C,
+                      cudaStream_t st);
+void launch_loss_grad(const float *Y, int Kp, const float *T, int K, const int *idx, int B,
+                      float *G, uint16_t *Gb, uint16_t *Gbt, double *loss, cudaStream_t st);
+void launch_colsum(const float *G, int R, int C, float *out, cudaStream_t st);
+struct AdamArgs {
+  float lr, b1, om1, b2, om2, eps, c1, c2;
+};
+void launch_adam(float *p, const float *g, float *m, float *v, int rows, int cols,
+                 const AdamArgs &a, uint16_t *wb, uint16_t *wt, cudaStream_t st);
+void launch_to_bf16(const float *p, int rows, int cols, uint16_t *wb, uint16_t *wt,
+                    cudaStream_t st);
+void launch_mlp_fwd(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
+                    const float *pcprof, const float *delta, int *status, int grid,
+                    cudaStream_t st);
+
 // thread-local error message
 void set_error(const std::string &msg);
+
+// Digits of a raw index packed 4 bits per parameter (last parameter fastest
+// in the raw order), and the constraint check on packed digits.
+uint64_t host_pack(const ktune_space *s, int64_t raw);
+bool host_valid(const ktune_space *s, uint64_t p);
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return KTUNE_ENOMEM;
+  }
+  return KTUNE_OK;
+}
 
 }  // namespace ktune
 
@@ -289,4 +353,46 @@ struct ktune_search {
   float *h_out_score = nullptr;
   uint64_t *h_out_packed = nullptr;
   int *h_nout = nullptr;
+};
+
+struct ktune_mlp {
+  ktune_space *space = nullptr;
+  int device = 0;
+  int P = 0, F = 0, K = 0, Kp = 0, Bmax = 0;
+  std::vector<int> roles;
+  std::vector<float> range;
+  std::vector<int> off;                 // [P + 1]
+  cudaStream_t stream = nullptr;
+  // float32 master parameters, gradients and Adam moments, 8 tensors:
+  // W1 256 x F, b1, W2 256 x 256, b2, W3, b3, W4 Kp x 256 (rows >= K zero), b4 [Kp]
+  float *d_p[8] = {}, *d_g[8] = {}, *d_m[8] = {}, *d_v[8] = {};
+  uint16_t *d_wb[4] = {}, *d_wt[4] = {};   // bf16 copies and transposes (d_wt[0] unused)
+  float *d_range = nullptr;
+  int *d_off = nullptr;
+  uint16_t *d_utab = nullptr;
+  int adam_t = 0;
+  // training set
+  uint64_t *d_data = nullptr;
+  float *d_target = nullptr;            // counters / range, [n][K]
+  int64_t n_data = 0, cap_data = 0;
+  // batch work buffers
+  int *d_idx = nullptr;
+  int64_t cap_idx = 0;
+  uint16_t *d_X = nullptr, *d_Xt = nullptr;
+  float *d_Z[3] = {};
+  uint16_t *d_A[3] = {}, *d_At[3] = {};
+  float *d_Y = nullptr, *d_G = nullptr;
+  uint16_t *d_Gb = nullptr, *d_Gbt = nullptr;
+  float *d_Gz[2] = {};
+  uint16_t *d_Gzb[2] = {}, *d_Gzbt[2] = {};
+  double *d_loss = nullptr;
+  int *d_status = nullptr;
+  // prediction staging
+  uint64_t *d_pred_in = nullptr;
+  float *d_pred_out = nullptr;
+  int64_t cap_pred = 0;
+
+  int rows(int t) const { return t == 0 || t == 2 || t == 4 ? 256 : t == 6 ? Kp : 1; }
+  int cols(int t) const { return t == 0 ? F : t == 7 ? Kp : 256; }
+  ktune::MlpDev dev() const;
 };

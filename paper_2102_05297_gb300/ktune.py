@@ -77,6 +77,18 @@ _SIGS = {
     "ktune_batch_variant": ([C.c_int, _i32p, _i32p, _i32p], C.c_int),
     "ktune_score_noalloc": ([_vp, C.c_int64, _vp, _vp, _vp, C.c_int, C.c_int, _i32p, _vp,
                              C.c_uint64, C.c_double, C.c_double, _vp, _vp, _vp], C.c_int),
+    "ktune_mlp_create": ([_vp, C.c_int, _i32p, _f32p, C.c_int, _vp, C.POINTER(_vp)], C.c_int),
+    "ktune_mlp_destroy": ([_vp], C.c_int),
+    "ktune_mlp_info": ([_vp, _i32p, _i64p], C.c_int),
+    "ktune_mlp_set_params": ([_vp, _f32p], C.c_int),
+    "ktune_mlp_get_params": ([_vp, _f32p], C.c_int),
+    "ktune_mlp_set_data": ([_vp, _i64p, _f32p, C.c_int64], C.c_int),
+    "ktune_mlp_grads": ([_vp, _i32p, C.c_int, C.POINTER(C.c_double), _f32p], C.c_int),
+    "ktune_mlp_train": ([_vp, _i32p, C.c_int, C.c_int, C.c_float, C.POINTER(C.c_double)], C.c_int),
+    "ktune_mlp_predict": ([_vp, _i64p, C.c_int64, _f32p], C.c_int),
+    "ktune_mlp_predict_device": ([_vp, C.c_int64, C.c_int64, _vp, _vp], C.c_int),
+    "ktune_gemm_bf16": ([_vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int,
+                         _vp], C.c_int),
 }
 EXPORTED = list(_SIGS)
 for _n, (_a, _r) in _SIGS.items():
@@ -329,3 +341,110 @@ class Batch:
             self.h = None
 
     __del__ = close
+
+
+# ---------------------------------------------------------------------------
+MLP_HIDDEN = 256
+
+
+class Mlp:
+    """Owns a ktune_mlp handle (the MLP counter model, trained on the GPU).
+
+    Parameters travel as a dict of float32 arrays W1 [256, F], b1 [256], W2,
+    b2, W3, b3, W4 [K, 256], b4 [K], flattened in that order for the C call."""
+
+    NAMES = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+
+    def __init__(self, space: Space, roles, ranges, max_batch: int = 4096, stream=None):
+        roles_a, roles_p = _arr(roles, np.int32)
+        rng_a, rng_p = _arr(ranges, np.float32)
+        h = C.c_void_p()
+        check(lib.ktune_mlp_create(space.h, len(roles_a), roles_p, rng_p, max_batch,
+                                   _stream_ptr(stream), C.byref(h)), "ktune_mlp_create")
+        self.h = h
+        self.space = space
+        self.K = len(roles_a)
+        f, n = C.c_int(), C.c_int64()
+        check(lib.ktune_mlp_info(h, C.byref(f), C.byref(n)), "ktune_mlp_info")
+        self.F, self.n_params = f.value, n.value
+
+    def shapes(self):
+        H, F, K = MLP_HIDDEN, self.F, self.K
+        return {"W1": (H, F), "b1": (H,), "W2": (H, H), "b2": (H,), "W3": (H, H), "b3": (H,),
+                "W4": (K, H), "b4": (K,)}
+
+    def _flat(self, params) -> np.ndarray:
+        sh = self.shapes()
+        parts = []
+        for k in self.NAMES:
+            a = np.asarray(params[k], dtype=np.float32)
+            if a.shape != sh[k]:
+                raise ValueError("%s has shape %s, expected %s" % (k, a.shape, sh[k]))
+            parts.append(a.ravel())
+        return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+
+    def _unflat(self, flat) -> dict:
+        out, o = {}, 0
+        for k in self.NAMES:
+            shp = self.shapes()[k]
+            n = int(np.prod(shp))
+            out[k] = flat[o:o + n].reshape(shp).copy()
+            o += n
+        return out
+
+    def set_params(self, params: dict):
+        flat = self._flat(params)
+        check(lib.ktune_mlp_set_params(self.h, flat.ctypes.data_as(_f32p)), "ktune_mlp_set_params")
+
+    def get_params(self) -> dict:
+        flat = np.empty(self.n_params, dtype=np.float32)
+        check(lib.ktune_mlp_get_params(self.h, flat.ctypes.data_as(_f32p)), "ktune_mlp_get_params")
+        return self._unflat(flat)
+
+    def set_data(self, raw, counters):
+        raw_a, raw_p = _arr(raw, np.int64)
+        c_a, c_p = _arr(np.asarray(counters, dtype=np.float32).reshape(len(raw_a), self.K),
+                        np.float32)
+        check(lib.ktune_mlp_set_data(self.h, raw_p, c_p, len(raw_a)), "ktune_mlp_set_data")
+
+    def grads(self, idx):
+        idx_a, idx_p = _arr(idx, np.int32)
+        loss = C.c_double()
+        flat = np.empty(self.n_params, dtype=np.float32)
+        check(lib.ktune_mlp_grads(self.h, idx_p, len(idx_a), C.byref(loss),
+                                  flat.ctypes.data_as(_f32p)), "ktune_mlp_grads")
+        return loss.value, self._unflat(flat)
+
+    def train(self, idx, batch: int, lr: float = 1e-3, return_losses: bool = True):
+        idx_a, idx_p = _arr(idx, np.int32)
+        steps = len(idx_a) // batch
+        losses = np.zeros(max(steps, 1), dtype=np.float64)
+        check(lib.ktune_mlp_train(self.h, idx_p, batch, steps, lr,
+                                  losses.ctypes.data_as(C.POINTER(C.c_double))
+                                  if return_losses else None), "ktune_mlp_train")
+        return losses[:steps]
+
+    def predict(self, raw) -> np.ndarray:
+        raw_a, raw_p = _arr(raw, np.int64)
+        out = np.empty((len(raw_a), self.K), dtype=np.float32)
+        check(lib.ktune_mlp_predict(self.h, raw_p, len(raw_a), out.ctypes.data_as(_f32p)),
+              "ktune_mlp_predict")
+        return out
+
+    def predict_device(self, first: int, count: int, out_ptr: int, stream=None):
+        check(lib.ktune_mlp_predict_device(self.h, first, count, out_ptr, _stream_ptr(stream)),
+              "ktune_mlp_predict_device")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ktune_mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+def gemm_bf16(a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, M: int, N: int,
+              Kd: int, stream=None):
+    """C = A B^T on the tensor cores (device pointers; see ktune_gemm_bf16)."""
+    check(lib.ktune_gemm_bf16(a_ptr, lda, b_ptr, ldb, c_ptr, ldc, M, N, Kd, _stream_ptr(stream)),
+          "ktune_gemm_bf16")

@@ -1,0 +1,194 @@
+"""The MLP counter model on the tensor cores against the oracle MLP.
+
+The GPU accumulates bfloat16 products in float32 on the tensor cores in its
+own order, the oracle in float64 and rounds once, so parity is within a
+tolerance: GEMMs within K 2^-22 of sum |a b| per element (float32 accumulation
+of K products), predictions, loss and gradients within the bounds written in
+each test (they allow rare one-ulp bfloat16 flips of intermediate
+activations where the two accumulation orders straddle a rounding boundary)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads.synth import SyntheticGPU, add_noise
+from oracle import mlp as omlp, space as ospace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kt():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2102_05297_gb300 import ktune
+    return ktune
+
+
+def bf16_tensor(torch, a):
+    return torch.from_numpy(omlp.bf16(a)).to(torch.bfloat16).cuda().contiguous()
+
+
+@pytest.mark.parametrize("M,N,Kd", [(128, 256, 64), (200, 48, 80), (300, 400, 128), (1, 16, 16),
+                                    (513, 272, 208), (64, 256, 4096)])
+def test_gemm_matches_float64(kt, M, N, Kd):
+    import torch
+    rng = np.random.default_rng(M * 7 + N + Kd)
+    a = omlp.bf16(rng.standard_normal((M, Kd)).astype(np.float32))
+    b = omlp.bf16(rng.standard_normal((N, Kd)).astype(np.float32))
+    ta, tb = bf16_tensor(torch, a), bf16_tensor(torch, b)
+    tc = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    kt.gemm_bf16(ta.data_ptr(), Kd, tb.data_ptr(), Kd, tc.data_ptr(), N, M, N, Kd)
+    got = tc.cpu().numpy()
+    ref = a.astype(np.float64) @ b.astype(np.float64).T
+    bound = Kd * 2.0 ** -22 * (np.abs(a).astype(np.float64) @ np.abs(b).astype(np.float64).T)
+    assert np.all(np.abs(got - ref) <= bound + 1e-30)
+
+
+def test_gemm_rejects_bad_shapes(kt):
+    with pytest.raises(kt.KtuneError):
+        kt.gemm_bf16(16, 24, 16, 24, 16, 16, 16, 16, 24)   # Kd not a multiple of 16
+    with pytest.raises(kt.KtuneError):
+        kt.gemm_bf16(16, 12, 16, 16, 16, 16, 16, 16, 16)   # lda not a multiple of 8
+
+
+def tiny_setup(K=16, seed=0):
+    desc = W.space_tiny_block_tile()
+    roles = W.layout(K)
+    gpu = SyntheticGPU(desc, roles, seed=seed)
+    valid = ospace.enumerate_valid(desc)
+    dig = ospace.decode(desc.radices, valid)
+    C, _ = gpu.evaluate(dig)
+    return desc, roles, gpu, valid, dig, C
+
+
+def random_params(F, K, seed):
+    p = omlp.init_params(F, K, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    for k in ("b1", "b2", "b3", "b4"):
+        p[k] = (rng.standard_normal(p[k].shape) * 0.1).astype(np.float32)
+    return p
+
+
+def test_features_width_matches_oracle(kt):
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=256)
+    assert m.F == omlp.n_features(desc.radices)
+    assert m.n_params == sum(int(np.prod(s)) for s in m.shapes().values())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_predict_matches_oracle(kt, seed):
+    desc, roles, gpu, valid, dig, C = tiny_setup(seed=seed)
+    ranges = gpu.counter_ranges()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, ranges, max_batch=256)
+    p = random_params(m.F, len(roles), seed)
+    m.set_params(p)
+    back = m.get_params()
+    for k in p:
+        np.testing.assert_array_equal(back[k], p[k])
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(len(valid), size=300, replace=False))   # 3 tiles, ragged tail
+    got = m.predict(valid[pick])
+    ref = omlp.predict(p, desc.values, dig[pick], ranges)
+    # a one-ulp bfloat16 flip of an activation moves it by 2^-8 relative; a few
+    # per row bound the worst element near 5e-3 of the counter's scale
+    scale = np.max(np.abs(ref), axis=0) + 1e-6
+    err = np.max(np.abs(got - ref), axis=0) / scale
+    assert np.all(err <= 5e-3), err
+    rms = np.sqrt(np.mean((got - ref) ** 2, axis=0)) / scale
+    assert np.all(rms <= 1e-3), rms
+
+
+def test_predict_device_matches_predict(kt):
+    import torch
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=256)
+    m.set_params(random_params(m.F, len(roles), 3))
+    n = len(valid)
+    out = torch.empty((n, len(roles)), dtype=torch.float32, device="cuda")
+    m.predict_device(0, n, out.data_ptr())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), m.predict(valid))
+
+
+@pytest.mark.parametrize("B", [64, 272])
+def test_grads_match_oracle(kt, B):
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    ranges = gpu.counter_ranges()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, ranges, max_batch=512)
+    p = random_params(m.F, len(roles), 7)
+    m.set_params(p)
+    rng = np.random.default_rng(B)
+    rows = rng.choice(len(valid), size=600, replace=False)
+    Cn = add_noise(C[rows], seed=1)
+    m.set_data(valid[rows], Cn)
+    idx = rng.choice(600, size=B, replace=False).astype(np.int32)
+    loss, g = m.grads(idx)
+    x = omlp.features(desc.values, dig[rows[idx]])
+    t = (Cn[idx] / ranges).astype(np.float32)
+    oloss, og = omlp.loss_and_grads(p, x, t)
+    assert abs(loss - oloss) <= 1e-3 * oloss
+    for k in og:
+        scale = float(np.max(np.abs(og[k]))) + 1e-12
+        err = float(np.max(np.abs(g[k] - og[k]))) / scale
+        assert err <= 2e-2, (k, err)
+        # the bulk agrees much more tightly than the worst element
+        rel = np.linalg.norm(g[k] - og[k]) / (np.linalg.norm(og[k]) + 1e-12)
+        assert rel <= 5e-3, (k, rel)
+
+
+def test_training_tracks_oracle_and_fits(kt):
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    ranges = gpu.counter_ranges()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, ranges, max_batch=256)
+    p = omlp.init_params(m.F, len(roles), seed=0)
+    m.set_params(p)
+    m.set_data(valid, C)
+    rng = np.random.default_rng(0)
+    steps, B = 150, 256
+    idx = np.concatenate([rng.choice(len(valid), size=B, replace=False) for _ in range(steps)])
+    losses = m.train(idx.astype(np.int32), B)
+    assert len(losses) == steps and np.all(np.isfinite(losses))
+    # the oracle trained on the same batches
+    x = omlp.features(desc.values, dig)
+    t = (C / ranges).astype(np.float32)
+    op = {k: v.copy() for k, v in p.items()}
+    opt = omlp.Adam(op)
+    olosses = []
+    for s in range(steps):
+        b = idx[s * B:(s + 1) * B]
+        l, g = omlp.loss_and_grads(op, x[b], t[b])
+        olosses.append(l)
+        opt.step(op, g)
+    olosses = np.array(olosses)
+    assert abs(losses[0] - olosses[0]) <= 1e-3 * olosses[0]
+    assert np.all(np.abs(losses - olosses) <= 0.1 * olosses + 1e-4), (losses[-5:], olosses[-5:])
+    base = float(np.mean((t - t.mean(axis=0)) ** 2))
+    final = m.predict(valid) / ranges
+    assert float(np.mean((final - t) ** 2)) < 0.5 * base
+
+
+def test_mlp_bad_arguments(kt):
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    sp = kt.Space.from_desc(desc)
+    with pytest.raises(kt.KtuneError):
+        kt.Mlp(sp, roles, np.zeros(len(roles)))                  # ranges must be > 0
+    with pytest.raises(kt.KtuneError):
+        kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=100)   # not a multiple of 16
+    m = kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=64)
+    with pytest.raises(kt.KtuneError):
+        m.grads(np.zeros(16, np.int32))                          # no training set yet
+    m.set_data(valid[:32], C[:32])
+    with pytest.raises(kt.KtuneError):
+        m.grads(np.zeros(80, np.int32))                          # beyond max_batch
+    with pytest.raises(kt.KtuneError):
+        m.grads(np.full(16, 32, np.int32))                       # row out of range
+    bad = np.array([1], np.int64)
+    if not np.isin(1, valid):
+        with pytest.raises(kt.KtuneError):
+            m.set_data(bad, C[:1])                               # invalid configuration
