@@ -314,6 +314,14 @@ int ktune_mlp_predict(ktune_mlp *m, const int64_t *raw, int64_t n, float *out);
  * (materialised spaces); enqueued on `stream`. */
 int ktune_mlp_predict_device(ktune_mlp *m, int64_t first, int64_t count, float *out, void *stream);
 
+/* A model handle that predicts with this MLP, for ktune_search_create: every
+ * step then predicts c_profile and scores all of TS through the fused
+ * tensor-core forward (a6-a8 on the MLP).  Needs a materialised space and
+ * KTUNE_SELECT_SAMPLE.  The MLP is not owned: keep it alive while the model
+ * and its searches exist; training between steps changes later steps'
+ * predictions.  Not accepted by ktune_batch_create. */
+int ktune_model_from_mlp(ktune_mlp *m, ktune_model **out);
+
 /* The tensor-core GEMM the MLP trains with, exposed for validation (no
  * counterpart in the paper): C[M][N] = A[M][Kd] * B[N][Kd]^T, all device
  * buffers, A and B bfloat16 bit patterns (uint16) row-major with leading

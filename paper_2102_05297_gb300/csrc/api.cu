@@ -602,6 +602,10 @@ int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model
 
 int ktune_model_destroy(ktune_model *m) {
   if (!m) return KTUNE_OK;
+  if (m->kind == 2) {   // the MLP is the caller's
+    delete m;
+    return KTUNE_OK;
+  }
   cudaFree(m->d_nodes);
   cudaFree(m->d_leaves);
   delete m;
@@ -621,6 +625,7 @@ int ktune_model_predict_device(const ktune_model *m, int64_t first, int64_t coun
   const ktune_space *s = m->space;
   if (!s->d_packed) FAIL(KTUNE_ESTATE, "space is not materialised");
   if (first < 0 || count < 0 || first + count > s->n_valid) FAIL(KTUNE_EINVAL, "range out of TS");
+  if (m->kind == 2) return ktune_mlp_predict_device(m->mlp, first, count, out, stream);
   launch_predict_full(s->d_packed + first, count, m->d_nodes, m->d_leaves, m->K, m->D, out,
                       (cudaStream_t)stream);
   CK(cudaGetLastError());
@@ -639,6 +644,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   if (!(o->inst_reaction >= 0.0 && o->inst_reaction < 1.0)) FAIL(KTUNE_EINVAL, "inst_reaction not in [0,1)");
   if (!(o->cores > 0.0) || !isfinite(o->gamma)) FAIL(KTUNE_EINVAL, "bad cores or gamma");
   if (s->n_valid == 0) FAIL(KTUNE_EXHAUSTED, "empty tuning space");
+  if (m->kind == 2 && (!s->d_packed || o->select != KTUNE_SELECT_SAMPLE))
+    FAIL(KTUNE_ESTATE, "MLP models need a materialised space and KTUNE_SELECT_SAMPLE");
   const bool otf = s->flags == KTUNE_ON_THE_FLY;
   if (otf && !s->narrow)
     FAIL(KTUNE_ESTATE, "on-the-fly spaces need all digits in one 32-bit word (sum of ceil(log2 n_values) <= 32)");
@@ -695,7 +702,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
       cudaMallocHost((void **)&h->h_out_raw, KTUNE_MAX_K * 8) != cudaSuccess ||
       cudaMallocHost((void **)&h->h_out_score, KTUNE_MAX_K * 4) != cudaSuccess ||
       cudaMallocHost((void **)&h->h_out_packed, KTUNE_MAX_K * 8) != cudaSuccess ||
-      cudaMallocHost((void **)&h->h_nout, 4) != cudaSuccess) {
+      cudaMallocHost((void **)&h->h_nout, 8) != cudaSuccess) {
     set_error("pinned host allocation failed");
     return fail(KTUNE_ENOMEM);
   }
@@ -839,10 +846,21 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
     else cudaEventRecord(h->ev[i], st);
   };
   mark(0);
-  launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
-  mark(1);
-  launch_bscore(h->d_srch, h->d_steps, h->d_items, h->n_items, h->mode,
-                h->opts.select == KTUNE_SELECT_TOPK, h->grid, st);
+  if (m->kind == 2) {
+    // MLP: set-up, prediction of c_profile, then predict + score all of TS
+    const MlpDev md = m->mlp->dev();
+    launch_mlp_prep(h->d_srch, h->d_steps, sb, st);
+    launch_mlp_fwd(0, md, &h->d_steps[0].cprof_packed, 1, h->d_pcprof, nullptr, nullptr, nullptr,
+                   nullptr, m->mlp->d_status, 1, st);
+    mark(1);
+    launch_mlp_fwd(1, md, h->space->d_packed, h->space->n_valid, h->d_s, h->d_pcprof, h->d_delta,
+                   h->d_eval, h->d_mm, m->mlp->d_status, h->num_sms, st);
+  } else {
+    launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
+    mark(1);
+    launch_bscore(h->d_srch, h->d_steps, h->d_items, h->n_items, h->mode,
+                  h->opts.select == KTUNE_SELECT_TOPK, h->grid, st);
+  }
   mark(2);
   if (h->opts.select == KTUNE_SELECT_SAMPLE) launch_bweights(h->d_srch, h->d_sub_search, h->n_sub, st);
   mark(3);
@@ -870,7 +888,7 @@ static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st)
       if (t != cudaGraphNodeTypeKernel) continue;
       cudaKernelNodeParams kp{};
       CK(cudaGraphKernelNodeGetParams(nd, &kp));
-      if (kp.func == bprep_func<1>()) h->prep_node = nd;
+      if (kp.func == bprep_func<1>() || kp.func == mlp_prep_func()) h->prep_node = nd;
     }
     if (!h->prep_node) FAIL(KTUNE_ECUDA, "graph capture lost the prepare kernel");
     CK(cudaGraphInstantiate(&h->gexec, g, 0));
@@ -926,7 +944,13 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
   CK(cudaMemcpyAsync(h->h_out_score, h->d_out_score, k * 4, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_out_packed, h->d_out_packed, k * 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_nout, h->d_nout, 4, cudaMemcpyDeviceToHost, h->stream));
+  if (h->model->kind == 2)
+    CK(cudaMemcpyAsync(h->h_nout + 1, h->model->mlp->d_status, 4, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->model->kind == 2 && h->h_nout[1]) {
+    cudaMemset(h->model->mlp->d_status, 0, 4);
+    FAIL(KTUNE_ETIMEOUT, "a tensor-core wait of the MLP timed out");
+  }
   const int n = *h->h_nout;
   *n_out = n;
   memcpy(out_raw, h->h_out_raw, n * 8);
@@ -1124,6 +1148,7 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!searches[i]) FAIL(KTUNE_EINVAL, "null search");
+    if (searches[i]->model->kind != 1) FAIL(KTUNE_ESTATE, "batches take tree models only");
     if (searches[i]->mode != searches[0]->mode || searches[i]->opts.select != searches[0]->opts.select)
       FAIL(KTUNE_EINVAL, "searches of a batch must share the space mode and the select mode");
   }

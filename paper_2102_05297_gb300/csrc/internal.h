@@ -214,8 +214,13 @@ void launch_adam(float *p, const float *g, float *m, float *v, int rows, int col
 void launch_to_bf16(const float *p, int rows, int cols, uint16_t *wb, uint16_t *wt,
                     cudaStream_t st);
 void launch_mlp_fwd(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
-                    const float *pcprof, const float *delta, int *status, int grid,
-                    cudaStream_t st);
+                    const float *pcprof, const float *delta, const uint32_t *evaluated,
+                    int *minmax, int *status, int grid, cudaStream_t st);
+void launch_mlp_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,
+                     cudaStream_t st);
+const void *mlp_prep_func();
+// Dynamic shared-memory limits of the MLP kernels (once per device, before use).
+void mlp_set_attrs(int F);
 
 // thread-local error message
 void set_error(const std::string &msg);
@@ -262,7 +267,8 @@ struct ktune_model {
   ktune_space *space = nullptr;
   int K = 0;
   int D = 0;
-  int kind = 1;
+  int kind = 1;                 // 1 trees, 2 MLP (not owned)
+  ktune_mlp *mlp = nullptr;
   std::vector<int> roles;
   uint8_t *d_nodes = nullptr;   // [K][2^D] node bytes (feature << 4 | threshold)
   float *d_leaves = nullptr;    // [K][2^D]

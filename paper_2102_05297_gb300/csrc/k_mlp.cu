@@ -38,6 +38,12 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
          z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
+// Order-preserving integer key of a float (for atomicMin / atomicMax).
+__device__ __forceinline__ int okey(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+
 __device__ __forceinline__ uint4 pack8(const uint16_t *h) {
   uint4 q;
   q.x = h[0] | ((uint32_t)h[1] << 16);
@@ -285,12 +291,15 @@ __device__ __forceinline__ void build_features(uint8_t *sX, const MlpDev &md, ui
 // MODE 0: out[i * K + c] = predicted counter c of configuration packed[i].
 // MODE 1: out[i] = Eq. score of configuration packed[i] against the profiled
 //         prediction pcprof and the expert system's delta (float32, counters
-//         ascending, the same operations as the tree path's term tables).
+//         ascending, the same operations as the tree path's term tables), and
+//         the minimum and maximum over entries whose `evaluated` bit is clear
+//         folded into minmax[0..1] (order-preserving integer keys).
 template <int MODE>
 __global__ void __launch_bounds__(128, 1)
     k_mlp_fwd(const MlpDev md, const uint64_t *__restrict__ packed, int64_t n,
               float *__restrict__ out, const float *__restrict__ pcprof,
-              const float *__restrict__ delta, int *status) {
+              const float *__restrict__ delta, const uint32_t *__restrict__ evaluated,
+              int *__restrict__ minmax, int *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t *sH = sm;                          // 128 x 256 activations (KC = 256)
   uint8_t *sW = sm + 65536;                  // 2 x (256 x 64) weight chunks
@@ -319,6 +328,7 @@ __global__ void __launch_bounds__(128, 1)
   bool pend[2] = {false, false};
   uint32_t g = 0;
   bool ok = true;
+  float s_mn = INFINITY, s_mx = -INFINITY;
   const int F = md.F;
   for (int64_t t0 = blockIdx.x * (int64_t)128; t0 < n && ok; t0 += (int64_t)gridDim.x * 128) {
     const int64_t i = t0 + threadIdx.x;
@@ -407,7 +417,13 @@ __global__ void __launch_bounds__(128, 1)
             }
           }
         }
-        if (i < n) out[i] = s;
+        if (i < n) {
+          out[i] = s;
+          if (!((evaluated[i >> 5] >> (i & 31)) & 1u)) {
+            s_mn = fminf(s_mn, s);
+            s_mx = fmaxf(s_mx, s);
+          }
+        }
       }
       tc::fence_before();
       __syncthreads();
@@ -418,10 +434,44 @@ __global__ void __launch_bounds__(128, 1)
     for (int b = 0; b < 2; ++b)
       if (pend[b]) tc::mbar_wait(&mbar[b], ph[b], kWaitLimit);
     if (threadIdx.x == 0) atomicExch(status, KTUNE_ETIMEOUT);
+  } else if (MODE == 1) {
+    for (int o = 16; o; o >>= 1) {
+      s_mn = fminf(s_mn, __shfl_xor_sync(0xffffffffu, s_mn, o));
+      s_mx = fmaxf(s_mx, __shfl_xor_sync(0xffffffffu, s_mx, o));
+    }
+    if ((threadIdx.x & 31) == 0 && s_mn <= s_mx) {
+      atomicMin(minmax, okey(s_mn));
+      atomicMax(minmax + 1, okey(s_mx));
+    }
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// Per-step set-up of a search scored by the MLP (one CTA): publish the step's
+// by-value parameters, Delta, reset the min / max keys, the output count and
+// the super-tile sums, and count the counters with a non-zero Delta.  Same
+// parameter list as the tree path's prepare kernel.
+__global__ void __launch_bounds__(256) k_mlp_prep(const SearchDev *__restrict__ srch,
+                                                  StepDev *__restrict__ steps_dev,
+                                                  const __grid_constant__ StepBatch<1> sb) {
+  const SearchDev &sd = srch[0];
+  const StepDev &st = sb.st[0];
+  if (threadIdx.x == 0) {
+    steps_dev[0] = st;
+    sd.mm[0] = INT_MAX;
+    sd.mm[1] = INT_MIN;
+    if (st.n_out) *st.n_out = 0;
+    int na = 0;
+    for (int c = 0; c < sd.K; ++c) na += st.delta[c] != 0.0f;
+    *sd.n_active = na;
+  }
+  for (int c = threadIdx.x; c < sd.K; c += blockDim.x) sd.delta[c] = st.delta[c];
+  if (sd.select == KTUNE_SELECT_SAMPLE) {
+    const int64_t n_super = ((sd.N + kSubTile - 1) / kSubTile + kSuper - 1) / kSuper;
+    for (int64_t i = threadIdx.x; i < n_super; i += blockDim.x) sd.super_sum[i] = 0;
+  }
 }
 
 }  // namespace
@@ -429,22 +479,27 @@ __global__ void __launch_bounds__(128, 1)
 // ---- host launchers -------------------------------------------------------------------------
 int mlp_fwd_smem(int F) { return 131072 + 256 * F; }
 
+void mlp_set_attrs(int F) {
+  cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  if (F > 0) {
+    const int smem = mlp_fwd_smem(kMlpMaxF);
+    cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
+}
+
 void launch_gemm_tc(int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
                     int K, const EpiArgs &ep, int *status, cudaStream_t st) {
   const dim3 grid((M + 127) / 128, (N + 255) / 256);
   switch (epi) {
-#define KT_CASE(E)                                                                              \
-  case E:                                                                                       \
-    cudaFuncSetAttribute(k_gemm_tc<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem); \
-    k_gemm_tc<E><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status);            \
-    break;
-    KT_CASE(0)
-    KT_CASE(1)
-    KT_CASE(2)
-    KT_CASE(3)
-#undef KT_CASE
-    default:
-      break;
+    case 0: k_gemm_tc<0><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status); break;
+    case 1: k_gemm_tc<1><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status); break;
+    case 2: k_gemm_tc<2><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status); break;
+    case 3: k_gemm_tc<3><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status); break;
+    default: break;
   }
 }
 
@@ -483,19 +538,25 @@ void launch_to_bf16(const float *p, int rows, int cols, uint16_t *wb, uint16_t *
 }
 
 void launch_mlp_fwd(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
-                    const float *pcprof, const float *delta, int *status, int grid,
-                    cudaStream_t st) {
+                    const float *pcprof, const float *delta, const uint32_t *evaluated,
+                    int *minmax, int *status, int grid, cudaStream_t st) {
   const int smem = mlp_fwd_smem(md.F);
   const int64_t tiles = (n + 127) / 128;
   if (tiles == 0) return;
   if (grid <= 0 || grid > tiles) grid = (int)tiles;
-  if (mode == 0) {
-    cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_mlp_fwd<0><<<grid, 128, smem, st>>>(md, packed, n, out, pcprof, delta, status);
-  } else {
-    cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_mlp_fwd<1><<<grid, 128, smem, st>>>(md, packed, n, out, pcprof, delta, status);
-  }
+  if (mode == 0)
+    k_mlp_fwd<0><<<grid, 128, smem, st>>>(md, packed, n, out, pcprof, delta, evaluated, minmax,
+                                          status);
+  else
+    k_mlp_fwd<1><<<grid, 128, smem, st>>>(md, packed, n, out, pcprof, delta, evaluated, minmax,
+                                          status);
 }
+
+void launch_mlp_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,
+                     cudaStream_t st) {
+  k_mlp_prep<<<1, 256, 0, st>>>(srch, steps_dev, sb);
+}
+
+const void *mlp_prep_func() { return (const void *)k_mlp_prep; }
 
 }  // namespace ktune

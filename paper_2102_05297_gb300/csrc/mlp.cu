@@ -248,6 +248,7 @@ int ktune_mlp_create(ktune_space *s, int K, const int32_t *roles, const float *r
   };
   int rc;
   cudaSetDevice(m->device);
+  mlp_set_attrs(F);
   for (int t = 0; t < 8; ++t) {
     const size_t n = (size_t)m->rows(t) * m->cols(t);
     if ((rc = dalloc(&m->d_p[t], n)) || (rc = dalloc(&m->d_g[t], n)) ||
@@ -503,8 +504,8 @@ int ktune_mlp_predict(ktune_mlp *m, const int64_t *raw, int64_t n, float *out) {
   }
   TRY(ensure_pred(m, n));
   CK(cudaMemcpyAsync(m->d_pred_in, packed.data(), (size_t)n * 8, cudaMemcpyHostToDevice, m->stream));
-  launch_mlp_fwd(0, m->dev(), m->d_pred_in, n, m->d_pred_out, nullptr, nullptr, m->d_status, 0,
-                 m->stream);
+  launch_mlp_fwd(0, m->dev(), m->d_pred_in, n, m->d_pred_out, nullptr, nullptr, nullptr, nullptr,
+                 m->d_status, 0, m->stream);
   CK(cudaGetLastError());
   TRY(finish(m));
   CK(cudaMemcpy(out, m->d_pred_out, (size_t)n * m->K * 4, cudaMemcpyDeviceToHost));
@@ -519,9 +520,24 @@ int ktune_mlp_predict_device(ktune_mlp *m, int64_t first, int64_t count, float *
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  launch_mlp_fwd(0, m->dev(), s->d_packed + first, count, out, nullptr, nullptr, m->d_status, sms,
-                 (cudaStream_t)stream);
+  launch_mlp_fwd(0, m->dev(), s->d_packed + first, count, out, nullptr, nullptr, nullptr, nullptr,
+                 m->d_status, sms, (cudaStream_t)stream);
   CK(cudaGetLastError());
+  return KTUNE_OK;
+}
+
+int ktune_model_from_mlp(ktune_mlp *mlp, ktune_model **out) {
+  if (!mlp || !out) FAIL(KTUNE_EINVAL, "null argument");
+  *out = nullptr;
+  ktune_model *m = new (std::nothrow) ktune_model();
+  if (!m) FAIL(KTUNE_ENOMEM, "host allocation");
+  m->space = mlp->space;
+  m->K = mlp->K;
+  m->D = 0;
+  m->kind = 2;
+  m->mlp = mlp;
+  m->roles = mlp->roles;
+  *out = m;
   return KTUNE_OK;
 }
 
@@ -532,6 +548,7 @@ int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, floa
   if ((lda & 7) || (ldb & 7) || lda < Kd || ldb < Kd || ldc < N) FAIL(KTUNE_EINVAL, "bad leading dimension");
   if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) FAIL(KTUNE_EINVAL, "A and B must be 16-byte aligned");
   int *status = nullptr;
+  mlp_set_attrs(0);
   TRY(dalloc(&status, 1));
   cudaStream_t st = (cudaStream_t)stream;
   cudaMemsetAsync(status, 0, 4, st);

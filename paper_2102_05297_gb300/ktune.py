@@ -87,6 +87,7 @@ _SIGS = {
     "ktune_mlp_train": ([_vp, _i32p, C.c_int, C.c_int, C.c_float, C.POINTER(C.c_double)], C.c_int),
     "ktune_mlp_predict": ([_vp, _i64p, C.c_int64, _f32p], C.c_int),
     "ktune_mlp_predict_device": ([_vp, C.c_int64, C.c_int64, _vp, _vp], C.c_int),
+    "ktune_model_from_mlp": ([_vp, C.POINTER(_vp)], C.c_int),
     "ktune_gemm_bf16": ([_vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int,
                          _vp], C.c_int),
 }
@@ -198,6 +199,20 @@ class Space:
 
 
 class Model:
+    """Owns a ktune_model handle: a tree ensemble (dict, see model_blob) or,
+    through ``Model.from_mlp``, a view of an Mlp."""
+
+    @classmethod
+    def from_mlp(cls, mlp: "Mlp") -> "Model":
+        self = cls.__new__(cls)
+        h = C.c_void_p()
+        check(lib.ktune_model_from_mlp(mlp.h, C.byref(h)), "ktune_model_from_mlp")
+        self.h = h
+        self.space = mlp.space
+        self.mlp = mlp            # keeps the MLP alive as long as the model
+        self.K, self.depth = mlp.K, 0
+        return self
+
     def __init__(self, space: Space, model: dict):
         blob = model_blob(model)
         self._blob = C.create_string_buffer(blob, len(blob))

@@ -192,3 +192,108 @@ def test_mlp_bad_arguments(kt):
     if not np.isin(1, valid):
         with pytest.raises(kt.KtuneError):
             m.set_data(bad, C[:1])                               # invalid configuration
+
+
+# ---- searches scored by the MLP ------------------------------------------------------
+def exact_params(desc, F, K, seed):
+    """A network whose every intermediate value is exact in float32 and bfloat16
+    on both sides: integer one-hot weights and a bias of 16 keep every
+    pre-activation in [16, 64], where GELU(z) = z exactly (erf rounds to 1 in
+    float32 and float64); identity middle layers; output weights in 1/64 steps.
+    Predictions, scores and therefore the draws must then match bit for bit."""
+    rng = np.random.default_rng(seed)
+    H = omlp.HIDDEN
+    n_onehot = sum(desc.radices)
+    W1 = np.zeros((H, F), np.float32)
+    W1[:, :n_onehot] = rng.integers(0, 4, size=(H, n_onehot))
+    p = {"W1": W1, "b1": np.full(H, 16.0, np.float32),
+         "W2": np.eye(H, dtype=np.float32), "b2": np.zeros(H, np.float32),
+         "W3": np.eye(H, dtype=np.float32), "b3": np.zeros(H, np.float32),
+         "W4": (rng.integers(-2, 3, size=(K, H)) / 64.0).astype(np.float32),
+         "b4": np.full(K, 600.0, np.float32)}
+    return p
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mlp_search_exact_network_matches_oracle(kt, seed):
+    from oracle import search as osearch
+    desc, roles, gpu, valid, dig, C = tiny_setup(seed=seed)
+    ranges = gpu.counter_ranges()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, ranges, max_batch=64)
+    p = exact_params(desc, m.F, len(roles), seed)
+    m.set_params(p)
+    pred = omlp.predict(p, desc.values, dig, ranges)
+    # the network is exact: the GPU's predictions equal the oracle's bit for bit
+    np.testing.assert_array_equal(m.predict(valid), pred)
+    model = kt.Model.from_mlp(m)
+    s = kt.Search(sp, model, k=5, seed=seed)
+    o = osearch.OracleSearch(desc, {"roles": roles}, k=5, seed=seed, valid=valid, pred=pred)
+    assert s.current() == o.cprof_raw
+    for step in range(12):
+        c = gpu.evaluate(ospace.decode(desc.radices, [s.current()]))[0][0]
+        g_raw, g_sc = s.step(c)
+        o_raw, o_sc = o.step(c)
+        assert list(g_raw) == o_raw, step
+        np.testing.assert_array_equal(np.asarray(g_sc, np.float32), np.float32(o_sc))
+        rts = gpu.evaluate(ospace.decode(desc.radices, g_raw))[1]
+        s.report(rts)
+        o.report(list(rts))
+
+
+def test_mlp_search_random_network_scores(kt):
+    """A random network: the tensor cores' accumulation order moves
+    predictions by a few 1e-3 of a counter's scale, so scores are compared
+    within a tolerance (picks of the two sides may then differ)."""
+    from oracle import expert, score as oscore
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    ranges = gpu.counter_ranges()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, ranges, max_batch=64)
+    p = random_params(m.F, len(roles), 11)
+    # counters are positive: keep the predictions well above 0 (a + A near 0
+    # would make Eq. score unbounded and amplify any rounding difference)
+    p["W4"] = (p["W4"] * 0.1).astype(np.float32)
+    p["b4"] = (np.abs(p["b4"]) + 1.0).astype(np.float32)
+    m.set_params(p)
+    pred = omlp.predict(p, desc.values, dig, ranges)
+    model = kt.Model.from_mlp(m)
+    pos = {int(r): i for i, r in enumerate(valid)}
+    for seed in range(4):
+        s = kt.Search(sp, model, k=8, seed=seed)
+        s.set_timing(True)
+        cp = pos[s.current()]
+        c = gpu.evaluate(dig[cp:cp + 1])[0][0]
+        g_raw, g_sc = s.step(c)
+        d32 = expert.delta_vector(roles, c, 0.7, 1000.0).astype(np.float32)
+        o_s = oscore.score_fp32(pred[cp], pred, d32)
+        assert np.all(pred > 0)
+        # |d term| <= |delta| * 2 (A |da| + a |dA|) / (a + A)^2 <= |delta| * 4 eps for
+        # relative prediction errors eps; eps <= 1e-3 here
+        bound = 4e-3 * float(np.sum(np.abs(d32))) + 1e-6
+        assert len(set(g_raw)) == 8 and cp not in [pos[r] for r in g_raw]
+        for r, sc in zip(g_raw, g_sc):
+            assert abs(sc - o_s[pos[r]]) <= bound
+        st = s.stats()
+        free = np.ones(len(valid), bool)
+        free[cp] = False
+        assert abs(st.s_min - o_s[free].min()) <= bound
+        assert abs(st.s_max - o_s[free].max()) <= bound
+        assert st.n_active == int(np.count_nonzero(d32))
+
+
+def test_mlp_model_rules(kt):
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    ranges = gpu.counter_ranges()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, ranges, max_batch=64)
+    model = kt.Model.from_mlp(m)
+    with pytest.raises(kt.KtuneError):
+        kt.Search(sp, model, k=5, select=kt.KTUNE_SELECT_TOPK)
+    otf = kt.Space.from_desc(desc, flags=kt.KTUNE_ON_THE_FLY)
+    m2 = kt.Mlp(otf, roles, ranges, max_batch=64)
+    with pytest.raises(kt.KtuneError):
+        kt.Search(otf, kt.Model.from_mlp(m2), k=5)
+    s = kt.Search(sp, model, k=5)
+    with pytest.raises(kt.KtuneError):
+        kt.Batch([s])
