@@ -1,20 +1,38 @@
 """Benchmark of the counter-guided search step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--paths all|none|mlp,batch,large,tiny]
 
-Workload (default): the mid-size synthetic tuning space -- 12 parameters,
-41.3M raw / 2.26M valid configurations materialised on the device, 32 FP32
-counters, depth-12 regression trees per counter fitted on a 2% sample with 2%
-Gaussian noise, k = 5 weighted draws per step.  A step is one full pass of the
-hot path: bottleneck analysis and Delta-PC, prediction of c_profile and of
-every unevaluated configuration, Eq. score, normalisation, integer weights,
-k draws without replacement, evaluated-set update.
+Workload of the headline line: the mid-size synthetic tuning space -- 12
+parameters, 41.3M raw / 2.26M valid configurations materialised on the
+device, 32 FP32 counters, depth-12 regression trees per counter fitted on a
+2% sample with 2% Gaussian noise, k = 5 weighted draws per step.  A step is
+one full pass of the hot path: bottleneck analysis and Delta-PC, prediction
+of c_profile and of every unevaluated configuration, Eq. score,
+normalisation, integer weights, k draws without replacement, evaluated-set
+update.
 
 The per-step inputs (the measured counters of each step's c_profile) come
 from a recorded search over the synthetic performance function; the timed
 steps replay them from device memory (``value``), and the end-to-end leg
 replays them through the host API with its copies (``e2e``).  L2 is flushed
 between timed steps (a 256 MB write outside the timed region).
+
+``paths`` (same JSON line) measures the other forms of the step, each with
+the roofline of its dominant kernel:
+  mlp    the MLP counter model on the same space: trained on the GPU (Adam,
+         2000 steps x 4096 rows) on a 5% profile sample with 2% noise; its
+         counter RMSE and the tree model's on a 1% held-out sample against
+         the noise-free synthetic counters; search steps scored by the fused
+         tensor-core forward, and their speed against the tree path;
+  batch  64 concurrent searches (8 per space) over 8 spaces of 3.5k-988k
+         valid configurations, 6-14 parameters, K in {16, 32, 40}, depth-12
+         trees, one graph launch per step, kernel shape from the autotuner;
+  large  the 16-parameter space, 113M raw / 19.5M valid configurations
+         decoded on the fly every step (nothing materialised), 40 counters,
+         depth-12 trees, top-16 select;
+  tiny   the 6-parameter block/tile space (1,824 configurations), 16
+         counters, depth-8 trees fitted on a 10% sample: step latency.
 
 With --gpus N > 1 (torchrun), every rank runs an independent search on its
 own GPU (replicas; the step has no cross-GPU exchange).
@@ -42,6 +60,8 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
+ALL_PATHS = ("mlp", "batch", "large", "tiny")
+MLP_HIDDEN = 256
 
 
 def peaks():
@@ -50,7 +70,8 @@ def peaks():
         with open(p) as f:
             d = json.load(f)
         return d, "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
 
 
 def load_desc(wl):
@@ -68,6 +89,18 @@ def describe(name, wl, desc, n_valid):
             "l2": "flushed between timed steps (256 MB write outside the timed region)"}
 
 
+def alu_peak(props, pk):
+    """Node visits/s at full issue: SMs x 4 SMSPs x 32 lanes x max SM clock
+    over 4 instructions per visit (load, digit extract, compare, index)."""
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    return props.multi_processor_count * 4 * 32 * mhz * 1e6 / 4.0, mhz
+
+
+def mlp_flops_per_config(F, K):
+    H = MLP_HIDDEN
+    return 2.0 * (F * H + 2 * H * H + H * K)
+
+
 # ---------------------------------------------------------------------------
 class Clocks:
     """nvidia-smi sampling during the timed region."""
@@ -83,7 +116,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -128,7 +161,7 @@ def setup(kt, name, seed):
     from paper_2102_05297_gb300 import fit
     model = fit.fit_model(digits[samp], Y, wl["depth"], desc.radices, roles)
     m = kt.Model(sp, model)
-    return wl, desc, roles, gpu, sp, valid, digits, model, m
+    return wl, desc, roles, gpu, sp, valid, digits, model, m, samp
 
 
 def record(kt, sp, m, gpu, valid, digits, wl, seed, n_steps):
@@ -148,6 +181,36 @@ def record(kt, sp, m, gpu, valid, digits, wl, seed, n_steps):
     return traj
 
 
+def timed_device_steps(kt, torch, s, traj, lo, hi, k, stream, flush):
+    """Steps lo..hi-1 of a recorded trajectory on device buffers, each timed
+    with CUDA events on the step's stream, L2 flushed before each."""
+    out_raw = torch.empty(k, dtype=torch.int64, device="cuda")
+    out_sc = torch.empty(k, dtype=torch.float32, device="cuda")
+    n_out = torch.empty(1, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, kern_ms, visits, scored, n_active = [], np.zeros(4), 0, 0, []
+    for i in range(lo, hi):
+        flush.zero_()
+        s.set_profile(int(traj[i][0]))
+        e0.record(stream)
+        s.step_device(np.ascontiguousarray(traj[i][1], np.float32), k, out_raw.data_ptr(),
+                      out_sc.data_ptr(), n_out.data_ptr(), stream)
+        e1.record(stream)
+        st = s.stats()                  # synchronises
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms += np.array(st.kernel_ms[:4])
+        visits += st.n_scored * st.n_active * (st.depth + 1)
+        scored += st.n_scored
+        n_active.append(st.n_active)
+    return step_ms, kern_ms, visits, scored, n_active
+
+
+def untimed_device_steps(s, traj, lo, hi, k, bufs, stream):
+    for i in range(lo, hi):
+        s.set_profile(int(traj[i][0]))
+        s.step_device(np.ascontiguousarray(traj[i][1], np.float32), k, *bufs, stream)
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -162,7 +225,7 @@ def run_ours(args):
 
     name = args.workload
     seed = rank
-    wl, desc, roles, gpu, sp, valid, digits, model, m = setup(kt, name, seed)
+    wl, desc, roles, gpu, sp, valid, digits, model, m, samp = setup(kt, name, seed)
     K, Wu = args.steps, args.warmup
     traj = record(kt, sp, m, gpu, valid, digits, wl, seed, Wu + K)
     # a dedicated stream: steps on a non-default stream run as one captured CUDA graph
@@ -173,37 +236,22 @@ def run_ours(args):
     # ---- device-resident timed steps -------------------------------------
     s = kt.Search(sp, m, k=wl["k"], seed=seed, stream=stream)
     s.set_timing(True)
-    cnt_host = [np.ascontiguousarray(t[1], dtype=np.float32) for t in traj]
-    out_raw = torch.empty(wl["k"], dtype=torch.int64, device="cuda")
-    out_sc = torch.empty(wl["k"], dtype=torch.float32, device="cuda")
-    n_out = torch.empty(1, dtype=torch.int32, device="cuda")
-    for i in range(Wu):
-        s.set_profile(int(traj[i][0]))
-        s.step_device(cnt_host[i], wl["k"], out_raw.data_ptr(), out_sc.data_ptr(),
-                      n_out.data_ptr(), stream)
+    bufs = (torch.empty(wl["k"], dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(wl["k"], dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    step_ms, score_ms, kern_ms, visits, scored = [], [], np.zeros(4), 0, 0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for i in range(Wu, Wu + K):
-        flush.zero_()
-        s.set_profile(int(traj[i][0]))
-        e0.record(stream)
-        s.step_device(cnt_host[i], wl["k"], out_raw.data_ptr(), out_sc.data_ptr(),
-                      n_out.data_ptr(), stream)
-        e1.record(stream)
-        st = s.stats()                  # synchronises
-        step_ms.append(e0.elapsed_time(e1))
-        kern_ms += np.array(st.kernel_ms[:4])
-        score_ms.append(st.kernel_ms[1])
-        visits += st.n_scored * st.n_active * (st.depth + 1)
-        scored += st.n_scored
+    time.sleep(0.25)                    # the sampler's first reading lands in the timed region
+    step_ms, kern_ms, visits, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + K,
+                                                             wl["k"], stream, flush)
     torch.cuda.synchronize()
     ck = clocks.stop()
     t_total = sum(step_ms) / 1e3
+    score_s = kern_ms[1] / 1e3
     s.close()
 
     # ---- end to end through the host API ---------------------------------
@@ -229,16 +277,33 @@ def run_ours(args):
         t_total, t_e2e, scored_all = float(tt[0]), float(tt[1]), float(cnt[0])
     else:
         t_e2e, scored_all = sum(e2e_ms) / 1e3, float(scored)
+
+    pk, src = peaks()
+    props = torch.cuda.get_device_properties(local)
+    peak_visits, sm_mhz = alu_peak(props, pk)
+    achieved = visits / score_s
+
+    paths = {}
+    if rank == 0 and world == 1:
+        want = ALL_PATHS if args.paths == "all" else \
+            () if args.paths == "none" else tuple(args.paths.split(","))
+        ctx = dict(kt=kt, torch=torch, stream=stream, flush=flush, pk=pk, src=src, props=props,
+                   steps=K, warmup=Wu, mlp_train_steps=args.mlp_train_steps)
+        if "mlp" in want:
+            paths["mlp"] = path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, m, samp, traj,
+                                    tree_ms=1e3 * t_total / K)
+        if "batch" in want:
+            paths["batch"] = path_batch(ctx)
+        if "large" in want:
+            paths["large"] = path_large(ctx)
+        if "tiny" in want:
+            paths["tiny"] = path_tiny(ctx)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    pk, src = peaks()
-    props = torch.cuda.get_device_properties(local)
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_visits = props.multi_processor_count * 4 * 32 * sm_mhz * 1e6 / 4.0
-    achieved = visits / (sum(score_ms) / 1e3)
     bytes_h2d = wl["K"] * 4
     bytes_d2h = wl["k"] * (8 + 4 + 8) + 4
     line = {
@@ -259,7 +324,7 @@ def run_ours(args):
         "config": describe(name, wl, desc, len(valid)),
         "roofline": {
             "bound": "alu",
-            "kernel": "k_score_mat (tree walk + Eq. score)",
+            "kernel": "k_bscore (tree walk + Eq. score)",
             "achieved": achieved / 1e9,
             "peak": peak_visits / 1e9,
             "unit": "Gvisit/s",
@@ -275,11 +340,279 @@ def run_ours(args):
         "gpu_launches": 4 * K,
         "clocks": ck,
     }
+    if paths:
+        line["paths"] = paths
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, model, traj[Wu][1])
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def rmse_norm(pred, truth, ranges):
+    """Range-normalised counter RMSE over all counters and rows."""
+    d = (np.asarray(pred, np.float64) - truth) / ranges
+    return float(np.sqrt(np.mean(d * d)))
+
+
+def path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp, traj, tree_ms):
+    """The MLP counter model on the headline space: GPU training, counter
+    RMSE against the tree model, and search steps scored on the tensor cores."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    from paper_2102_05297_gb300 import fit
+    n = len(valid)
+    Kc = wl["K"]
+    ranges = gpu.counter_ranges()
+    samp = sample_indices(n, 0.05, 11)
+    Y = add_noise(gpu.evaluate(digits[samp])[0], 11, 0.02)
+    rest = np.setdiff1d(np.setdiff1d(np.arange(n), samp), tree_samp)
+    held = np.sort(np.random.default_rng(12).choice(rest, size=max(1, n // 100), replace=False))
+    truth = gpu.evaluate(digits[held])[0].astype(np.float64)
+
+    B, steps = 4096, ctx["mlp_train_steps"]
+    mlp = kt.Mlp(sp, roles, ranges, max_batch=B, stream=stream)
+    mlp.set_params(fit.init_mlp(mlp.F, Kc, seed=0))
+    mlp.set_data(valid[samp], Y)
+    rng = np.random.default_rng(13)
+    idx = rng.integers(0, len(samp), size=steps * B).astype(np.int32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = mlp.train(idx, B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    fpc = mlp_flops_per_config(mlp.F, Kc)
+    train_flops = 3.0 * fpc * B * steps
+
+    rm_mlp = rmse_norm(mlp.predict(valid[held]), truth, ranges)
+    pred_all = torch.empty((n, Kc), dtype=torch.float32, device="cuda")
+    tm = tree_model
+    tm.predict_device(0, n, pred_all.data_ptr(), stream)
+    torch.cuda.synchronize()
+    rm_tree = rmse_norm(pred_all[torch.from_numpy(held).cuda()].cpu().numpy(), truth, ranges)
+    del pred_all
+
+    model = kt.Model.from_mlp(mlp)
+    s = kt.Search(sp, model, k=wl["k"], seed=0, stream=stream)
+    s.set_timing(True)
+    Wu = ctx["warmup"]
+    n_steps = min(ctx["steps"], 100)
+    bufs = (torch.empty(wl["k"], dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(wl["k"], dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
+    torch.cuda.synchronize()
+    step_ms, kern_ms, _, scored, _ = timed_device_steps(kt, torch, s, traj, Wu,
+                                                        min(len(traj), Wu + n_steps), wl["k"],
+                                                        stream, flush)
+    s.close()
+    model.close()
+    mlp.close()
+    t = sum(step_ms) / 1e3
+    ns = len(step_ms)
+    score_s = kern_ms[1] / 1e3
+    pk = ctx["pk"]
+    peak = float(pk.get("bf16_tflops", 1933.0)) * 1e12
+    ach = scored * fpc / score_s
+    return {
+        "workload": "MLP %d->256->256->256->%d (GELU, BF16 operands, FP32 accumulate) on the "
+                    "mid_12p space; trained on the GPU with Adam, %d steps x %d rows, on a 5%% "
+                    "profile sample (%d configurations) + 2%% noise" % (mlp.F, Kc, steps, B, len(samp)),
+        "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / ns,
+        "steps_per_s": ns / t, "steps": ns,
+        "counter_rmse": {"mlp": rm_mlp, "tree": rm_tree,
+                         "definition": "range-normalised RMSE over all %d counters on a 1%% held-out "
+                                       "sample (%d configurations) against the noise-free synthetic "
+                                       "counters; trees: depth 12 on a 2%% sample" % (Kc, len(held))},
+        "speedup_vs_tree": tree_ms / (1e3 * t / ns),
+        "train": {"ms": train_ms, "final_loss": float(losses[-1]), "first_loss": float(losses[0]),
+                  "tflops": train_flops / (train_ms / 1e3) / 1e12,
+                  "flops": "3 x forward (%d FLOP per row) per row" % fpc},
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_fwd<score> (fused forward + Eq. score)",
+                     "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": None,
+                     "peak_source": "%s bf16 burst (cuBLAS GEMM)" % ctx["src"],
+                     "flop_per_config": fpc,
+                     "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
+                                      "score": kern_ms[1] / kern_ms.sum(),
+                                      "weights": kern_ms[2] / kern_ms.sum(),
+                                      "select": kern_ms[3] / kern_ms.sum()}},
+    }
+
+
+BATCH_SPACES = ["batch_%d" % i for i in range(8)]
+BATCH_K = [16, 32, 40, 32, 16, 40, 32, 16]
+
+
+def path_batch(ctx, per_space=8, depth=12):
+    kt, torch, stream = ctx["kt"], ctx["torch"], ctx["stream"]
+    from workloads.trees import random_model
+    entries = []
+    keep = []
+    for si, nm in enumerate(BATCH_SPACES):
+        d = W.load_space(nm)
+        roles = W.layout(BATCH_K[si])
+        model = random_model(d.radices, roles, depth=depth, seed=100 + si)
+        gpu = SyntheticGPU(d, roles, seed=si)
+        sp = kt.Space.from_desc(d)
+        m = kt.Model(sp, model)
+        valid = sp.valid_raw()
+        dig = sp.valid_digits()
+        keep += [sp, m]
+        for r in range(per_space):
+            s = kt.Search(sp, m, k=5, seed=10 * si + r, search_id=r, stream=stream)
+            entries.append((s, gpu, valid, dig))
+    n_valid = [len(e[2]) for e in entries[::per_space]]
+
+    def counters():
+        out = []
+        for s, gpu, valid, dig in entries:
+            p = int(np.searchsorted(valid, s.current()))
+            out.append(gpu.evaluate(dig[p:p + 1])[0][0])
+        return out
+
+    b = kt.Batch([e[0] for e in entries], stream=stream)
+    c0 = counters()
+    choice, ms = b.autotune(c0, reps=3)
+    n_steps = min(ctx["steps"], 100)
+    Wu = ctx["warmup"]
+    # the counters of every step are precomputed from a recording so that
+    # the timed loop holds only the batched steps
+    seqs = []
+    for i in range(Wu + n_steps):
+        c = counters()
+        res = b.step(c, 5)
+        seqs.append(c)
+        for (s, gpu, valid, dig), (raw, _) in zip(entries, res):
+            s.report(gpu.evaluate(dig[np.searchsorted(valid, raw)])[1])
+    b.close()
+    for s, *_ in entries:
+        s.close()
+    # replay: fresh searches, same counters, same c_profiles (reports follow
+    # the same runtimes, so the trajectory repeats exactly)
+    entries2 = []
+    for si, nm in enumerate(BATCH_SPACES):
+        sp, m = keep[2 * si], keep[2 * si + 1]
+        for r in range(per_space):
+            entries2.append(kt.Search(sp, m, k=5, seed=10 * si + r, search_id=r, stream=stream))
+    b = kt.Batch(entries2, stream=stream)
+    b.autotune(c0, reps=1)
+    scored, t_ms = 0, 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(Wu + n_steps):
+        n_before = sum(len(e[2]) - s.evaluated() for s, e in zip(entries2, entries))
+        e0.record(stream)
+        res = b.step(seqs[i], 5)        # host outputs: synchronises
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= Wu:
+            t_ms += e0.elapsed_time(e1)
+            scored += n_before
+        for s2, (s, gpu, valid, dig), (raw, _) in zip(entries2, entries, res):
+            s2.report(gpu.evaluate(dig[np.searchsorted(valid, raw)])[1])
+    b.close()
+    for s in entries2:
+        s.close()
+    thr, cpt, ipc = kt.Batch.variant(choice)
+    t = t_ms / 1e3
+    return {
+        "workload": "%d searches (%d per space) over %d spaces of %s valid configurations, "
+                    "K %s, depth-%d random trees, k=5 weighted draws; one CUDA-graph launch per "
+                    "batched step" % (len(entries), per_space, len(BATCH_SPACES),
+                                      "/".join(str(v) for v in n_valid),
+                                      "/".join(str(k) for k in BATCH_K), depth),
+        "value": scored / t, "unit": "configs/s", "ms_per_batch_step": t_ms / n_steps,
+        "search_steps_per_s": len(entries) * n_steps / t, "steps": n_steps,
+        "autotune": {"choice": choice, "threads": thr, "configs_per_thread": cpt,
+                     "items_per_cta": ipc, "candidates_ms": [float(x) for x in ms]},
+        "timing": "CUDA events around ktune_batch_step, including its device-to-host copy of "
+                  "the 64 searches' selections",
+    }
+
+
+def path_large(ctx, depth=12):
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    from workloads.trees import random_model
+    d = W.load_space("large_16p")
+    roles = W.layout(40)
+    model = random_model(d.radices, roles, depth=depth, seed=40)
+    gpu = SyntheticGPU(d, roles, seed=0)
+    sp = kt.Space.from_desc(d, flags=kt.KTUNE_ON_THE_FLY)
+    n_valid, n_raw = sp.count()
+    m = kt.Model(sp, model)
+    k = 16
+    n_steps = min(ctx["steps"], 50)
+    Wu = ctx["warmup"]
+
+    def dig_of(raw):
+        out = np.zeros((len(raw), d.n_params), np.int64)
+        for j, r in enumerate(raw):
+            v = sp.decode(int(r))
+            out[j] = [d.values[p].index(v[p]) for p in range(d.n_params)]
+        return out
+
+    rec = kt.Search(sp, m, k=k, seed=0, select=kt.KTUNE_SELECT_TOPK)
+    traj = []
+    for _ in range(Wu + n_steps):
+        cp = rec.current()
+        c = gpu.evaluate(dig_of([cp]))[0][0]
+        raw, _ = rec.step(c)
+        rec.report(gpu.evaluate(dig_of(raw))[1])
+        traj.append((cp, c))
+    rec.close()
+    s = kt.Search(sp, m, k=k, seed=0, select=kt.KTUNE_SELECT_TOPK, stream=stream)
+    s.set_timing(True)
+    bufs = (torch.empty(k, dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(k, dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+    torch.cuda.synchronize()
+    step_ms, kern_ms, visits, scored, nact = timed_device_steps(kt, torch, s, traj, Wu,
+                                                                Wu + n_steps, k, stream, flush)
+    s.close()
+    t = sum(step_ms) / 1e3
+    peak, _ = alu_peak(ctx["props"], ctx["pk"])
+    ach = visits / (kern_ms[1] / 1e3)
+    return {
+        "workload": "large_16p on the fly: %d raw / %d valid configurations decoded every step "
+                    "(none stored), K=40, depth-%d random trees, top-%d select" % (
+                        n_raw, n_valid, depth, k),
+        "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / n_steps,
+        "steps_per_s": n_steps / t, "steps": n_steps,
+        "raw_decoded_per_s": n_raw * n_steps / t,
+        "roofline": {"bound": "alu", "kernel": "k_bscore<on-the-fly> (decode + filter + walk + score)",
+                     "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "Gvisit/s",
+                     "frac": ach / peak, "traffic": None,
+                     "mean_active_counters": float(np.mean(nact)),
+                     "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
+                                      "score": kern_ms[1] / kern_ms.sum(),
+                                      "select": kern_ms[3] / kern_ms.sum()}},
+    }
+
+
+def path_tiny(ctx):
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    wl, desc, roles, gpu, sp, valid, digits, model, m, samp = setup(kt, "tiny_block_tile", 0)
+    n_steps = 40
+    Wu = ctx["warmup"]
+    traj = record(kt, sp, m, gpu, valid, digits, wl, 0, Wu + n_steps)
+    s = kt.Search(sp, m, k=5, seed=0, stream=stream)
+    bufs = (torch.empty(5, dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(5, dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    untimed_device_steps(s, traj, 0, Wu, 5, bufs, stream)
+    torch.cuda.synchronize()
+    step_ms, _, _, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + n_steps, 5,
+                                                  stream, flush)
+    s.close()
+    return {"workload": "tiny_block_tile: 6 params, %d valid configurations, K=16, depth-8 trees "
+                        "fitted on a 10%% sample, k=5; %d steps" % (len(valid), n_steps),
+            "us_per_step_median": 1e3 * statistics.median(step_ms),
+            "us_per_step_mean": 1e3 * sum(step_ms) / n_steps,
+            "value": scored / (sum(step_ms) / 1e3), "unit": "configs/s",
+            "bound": "launch latency (one CUDA-graph launch of 4 kernels per step)"}
 
 
 # ---------------------------------------------------------------------------
@@ -373,10 +706,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid_12p", choices=list(WORKLOADS))
+    ap.add_argument("--paths", default="all",
+                    help="all | none | comma list of %s" % ",".join(ALL_PATHS))
+    ap.add_argument("--mlp-train-steps", type=int, default=2000,
+                    help="Adam steps (4096 rows each) of the MLP path's training")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

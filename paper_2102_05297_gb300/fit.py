@@ -101,3 +101,19 @@ def fit_model(digits, Y, depth: int, radices: List[int], roles: List[int]) -> di
     Y = np.asarray(Y)
     return {"roles": list(roles), "depth": int(depth),
             "trees": [fit_tree(digits, Y[:, k], depth, radices) for k in range(Y.shape[1])]}
+
+
+def init_mlp(F: int, K: int, hidden: int = 256, seed: int = 0) -> dict:
+    """Seeded starting parameters of the MLP counter model (host tooling, as
+    the tree fitter is): every weight uniform in +-1/sqrt(fan_in) (the
+    classic fan-in scaling), biases zero."""
+    rng = np.random.default_rng(seed)
+
+    def w(rows, cols):
+        b = 1.0 / np.sqrt(cols)
+        return rng.uniform(-b, b, size=(rows, cols)).astype(np.float32)
+
+    return {"W1": w(hidden, F), "b1": np.zeros(hidden, np.float32),
+            "W2": w(hidden, hidden), "b2": np.zeros(hidden, np.float32),
+            "W3": w(hidden, hidden), "b3": np.zeros(hidden, np.float32),
+            "W4": w(K, hidden), "b4": np.zeros(K, np.float32)}
