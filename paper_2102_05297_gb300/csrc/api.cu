@@ -172,6 +172,80 @@ int build_groups(ktune_space *s, const int32_t *code, int n) {
   return KTUNE_OK;
 }
 
+// Window tables of the one-word layout (see WinDev): groups in program order
+// join the current window while the union of their parameters' digit widths
+// stays within kWinBits; each window's table holds, for every value of its
+// index, the AND of its groups' constraint bits (0 where a field is not a
+// digit of its parameter).
+void build_windows(ktune_space *s) {
+  const int G = (int)s->groups.size();
+  std::vector<std::vector<int>> members;   // groups per window
+  std::vector<uint32_t> pmask;             // parameters per window (bit mask)
+  auto width_of = [&](uint32_t m) {
+    int w = 0;
+    for (int j = 0; j < s->sa.P; ++j)
+      if ((m >> j) & 1u) w += s->width[j];
+    return w;
+  };
+  for (int g = 0; g < G; ++g) {
+    const GroupDev &gr = s->groups[g];
+    uint32_t m = 0;
+    for (int i = 0; i < gr.n; ++i) m |= 1u << gr.param[i];
+    if (width_of(m) > kWinBits) {
+      s->generic.push_back((uint8_t)g);
+      continue;
+    }
+    if (!members.empty() && width_of(pmask.back() | m) <= kWinBits) {
+      members.back().push_back(g);
+      pmask.back() |= m;
+    } else {
+      members.push_back({g});
+      pmask.push_back(m);
+    }
+  }
+  for (size_t w = 0; w < members.size(); ++w) {
+    WinDev wd{};
+    int bits = 0;
+    for (int j = 0; j < s->sa.P; ++j)
+      if ((pmask[w] >> j) & 1u) {
+        wd.pos[wd.n] = s->pos[j];
+        wd.mask[wd.n] = (uint8_t)((1u << s->width[j]) - 1u);
+        wd.dst[wd.n] = (uint8_t)bits;
+        bits += s->width[j];
+        ++wd.n;
+      }
+    const int words = bits >= 5 ? (1 << (bits - 5)) : 1;
+    if ((int)s->win.size() == kMaxWin || (int)s->win_table.size() + words > kWinWords) {
+      for (int g : members[w]) s->generic.push_back((uint8_t)g);
+      continue;
+    }
+    wd.bits = (uint8_t)bits;
+    wd.off = (uint16_t)s->win_table.size();
+    std::vector<uint32_t> tab(words, 0u);
+    for (uint32_t v = 0; v < (1u << bits); ++v) {
+      uint32_t W = 0;   // the word whose window index is v
+      for (int i = 0; i < wd.n; ++i)
+        W |= ((v >> wd.dst[i]) & wd.mask[i]) << wd.pos[i];
+      bool ok = true;
+      for (int g : members[w]) {
+        const GroupDev &gr = s->groups[g];
+        uint32_t sub = 0;
+        for (int i = 0; i < gr.n && ok; ++i) {
+          const int p = gr.param[i];
+          const uint32_t d = (W >> s->pos[p]) & ((1u << s->width[p]) - 1u);
+          if ((int)d >= s->sa.radix[p]) ok = false;
+          sub += d * gr.sub_stride[i];
+        }
+        if (ok) ok = (s->table[gr.off_words + (sub >> 5)] >> (sub & 31)) & 1u;
+        if (!ok) break;
+      }
+      if (ok) tab[v >> 5] |= 1u << (v & 31);
+    }
+    s->win.push_back(wd);
+    s->win_table.insert(s->win_table.end(), tab.begin(), tab.end());
+  }
+}
+
 }  // namespace
 
 namespace ktune {
@@ -370,10 +444,18 @@ int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune
     }
     s->narrow = bits <= 32;
   }
+  if (s->narrow) build_windows(s);
 
   cudaStream_t cs = (cudaStream_t)stream;
   if ((rc = dalloc(&s->d_groups, s->groups.size()))) return cleanup(rc);
   if ((rc = dalloc(&s->d_table, s->table.size()))) return cleanup(rc);
+  if ((rc = dalloc(&s->d_win_table, std::max<size_t>(1, s->win_table.size())))) return cleanup(rc);
+  if (!s->win_table.empty() &&
+      cudaMemcpyAsync(s->d_win_table, s->win_table.data(), s->win_table.size() * 4,
+                      cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess) {
+    set_error("descriptor upload failed");
+    return cleanup(KTUNE_ECUDA);
+  }
   if (!s->groups.empty()) {
     if (cudaMemcpyAsync(s->d_groups, s->groups.data(), s->groups.size() * sizeof(GroupDev),
                         cudaMemcpyHostToDevice, cs) != cudaSuccess ||
@@ -435,6 +517,7 @@ int ktune_space_destroy(ktune_space *s) {
   cudaFree(s->d_table);
   cudaFree(s->d_packed);
   cudaFree(s->d_narrow);
+  cudaFree(s->d_win_table);
   cudaFree(s->d_tile_offset);
   delete s;
   return KTUNE_OK;
@@ -719,6 +802,19 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   for (int j = 0; j < KTUNE_MAX_PARAMS; ++j) {
     sd.pos[j] = s->pos[j];
     sd.width[j] = s->width[j];
+  }
+  sd.win_table = s->d_win_table;
+  sd.n_win = (int)s->win.size();
+  sd.win_words = (int)s->win_table.size();
+  for (int w = 0; w < sd.n_win; ++w) sd.win[w] = s->win[w];
+  sd.n_generic = (int)s->generic.size();
+  for (int g = 0; g < sd.n_generic; ++g) sd.generic[g] = s->generic[g];
+  {
+    int64_t rem = 128;
+    for (int j = s->sa.P - 1; j >= 0; --j) {
+      sd.inc128[j] = (uint8_t)(rem % s->sa.radix[j]);
+      rem /= s->sa.radix[j];
+    }
   }
   sd.nodes = m->d_nodes;
   sd.leaves = m->d_leaves;

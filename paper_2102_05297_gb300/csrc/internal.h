@@ -65,6 +65,21 @@ constexpr int kSuper = 32;              // sub-tiles per super-tile (select hier
 constexpr int kMaxSuper = 4096;         // => at most 134M valid configurations per search
 constexpr int kOtfRun = 4;              // raw indices per thread per decode round (on-the-fly)
 
+// Constraint "window" tables of the one-word layout: constraint groups are
+// merged greedily while the digits of all their parameters fit kWinBits bits;
+// a window's bit table is indexed by those digits' bit fields concatenated,
+// and holds the AND of its groups' constraints.  Checking a decoded word is
+// then a few field extractions and one table bit per window.  A group wider
+// than kWinBits keeps the general per-parameter check.
+constexpr int kMaxWin = 16;             // window tables per space
+constexpr int kWinBits = 12;            // widest window index: 4096 bits
+constexpr int kWinWords = 2048;         // all window tables of a space, 32-bit words (8 KB)
+struct alignas(4) WinDev {
+  uint8_t n, bits;                      // parameters, index bits
+  uint16_t off;                         // first word of the table
+  uint8_t pos[kWinBits], mask[kWinBits], dst[kWinBits];   // (W >> pos) & mask -> index bits dst..
+};
+
 // Static description of one search, uploaded once.
 struct SearchDev {
   const uint64_t *packed;     // materialised TS, nibble layout (or null)
@@ -77,6 +92,13 @@ struct SearchDev {
   int select;                 // KTUNE_SELECT_*
   SpaceArgs sa;
   uint8_t pos[KTUNE_MAX_PARAMS], width[KTUNE_MAX_PARAMS];
+  // on-the-fly decode: window tables, the groups they leave out, and the
+  // digits of 128 in the space's mixed radix (last parameter fastest)
+  const uint32_t *win_table;
+  int n_win, win_words, n_generic;
+  WinDev win[kMaxWin];
+  uint8_t generic[kMaxGroups];
+  uint8_t inc128[KTUNE_MAX_PARAMS];
   const uint8_t *nodes;
   const float *leaves;
   int K, D;
@@ -261,6 +283,11 @@ struct ktune_space {
   uint32_t *d_narrow = nullptr;      // TS in the narrow layout (materialised, narrow spaces)
   int64_t *d_tile_offset = nullptr;  // exclusive valid prefix per raw tile (+ total)
   std::vector<int64_t> tile_offset;  // host copy (on-the-fly spaces)
+  // window tables of the one-word layout (narrow spaces)
+  std::vector<ktune::WinDev> win;
+  std::vector<uint32_t> win_table;
+  std::vector<uint8_t> generic;      // groups no window covers
+  uint32_t *d_win_table = nullptr;
 };
 
 struct ktune_model {

@@ -27,6 +27,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kOtfCap = 4096;                           // on-the-fly list capacity
 constexpr int kOtfBytes = kOtfCap * 12;                 // (W, ordinal, raw32)
+constexpr int kBScoreSmem = 225 * 1024;                  // dynamic shared memory of k_bscore
 constexpr int kSelB = 256;   // select CTA size (the draws themselves run in warp 0)
 
 __device__ __forceinline__ int okey(float f) {
@@ -259,6 +260,95 @@ __device__ __forceinline__ bool valid_word(const SearchDev &sd, uint32_t W) {
   return true;
 }
 
+// On-the-fly decode context, staged in shared memory per work item: the
+// one-word layout, the digits of 128 in the mixed radix, the window tables
+// (their words follow the struct) and the count of groups no window covers.
+struct OtfCtx {
+  uint8_t pos[KTUNE_MAX_PARAMS], width[KTUNE_MAX_PARAMS], radix[KTUNE_MAX_PARAMS],
+      inc[KTUNE_MAX_PARAMS];
+  WinDev win[kMaxWin];
+  int P, n_win, n_generic, inc_top;
+};
+constexpr int kCtxMax = ((int)sizeof(OtfCtx) + kWinWords * 4 + 15) & ~15;
+static_assert(sizeof(OtfCtx) % 16 == 0, "window tables start 16-byte aligned");
+
+// Word of raw index `raw` (digits by division, last parameter fastest).
+__device__ __forceinline__ uint32_t otf_decode(const OtfCtx *c, uint32_t raw) {
+  uint32_t W = 0;
+  for (int j = c->P - 1; j >= 0; --j) {
+    const uint32_t r = c->radix[j];
+    const uint32_t q = raw / r;
+    W |= (raw - q * r) << c->pos[j];
+    raw = q;
+  }
+  return W;
+}
+
+// Word of the next raw index (odometer step).
+__device__ __forceinline__ uint32_t otf_next(const OtfCtx *c, uint32_t W) {
+  for (int j = c->P - 1; j >= 0; --j) {
+    const uint32_t sh = c->pos[j], m = (1u << c->width[j]) - 1u;
+    const uint32_t d = ((W >> sh) & m) + 1u;
+    if (d < c->radix[j]) return W + (1u << sh);
+    W &= ~(m << sh);
+  }
+  return W;
+}
+
+// Word of the raw index 128 further on: digit-wise addition of 128's digits
+// with carry, stopping once no digit or carry is left.
+__device__ __forceinline__ uint32_t otf_add128(const OtfCtx *c, uint32_t W) {
+  uint32_t carry = 0;
+  for (int j = c->P - 1; j >= 0; --j) {
+    const uint32_t inc = c->inc[j] + carry;
+    if (inc == 0) {
+      if (j < c->inc_top) break;
+      continue;
+    }
+    const uint32_t sh = c->pos[j], m = (1u << c->width[j]) - 1u;
+    uint32_t d = ((W >> sh) & m) + inc;
+    carry = d >= c->radix[j] ? 1u : 0u;
+    if (carry) d -= c->radix[j];
+    W = (W & ~(m << sh)) | (d << sh);
+  }
+  return W;
+}
+
+// Validity of four decoded words (bit u of the result for Wq[u]; only the
+// first n count): every window's table bit, then the groups no window
+// covers.  A window's parameter fields are read once for all four words.
+__device__ __forceinline__ uint32_t otf_valid4(const OtfCtx *c, const SearchDev &sd,
+                                               const uint32_t (&Wq)[4], int n) {
+  const uint32_t *tab = reinterpret_cast<const uint32_t *>(c + 1);
+  uint32_t vm = n >= 4 ? 15u : (1u << n) - 1u;
+  for (int w = 0; w < c->n_win && vm; ++w) {
+    const WinDev &wd = c->win[w];
+    uint32_t x[4] = {0u, 0u, 0u, 0u};
+    for (int i = 0; i < wd.n; ++i) {
+      const uint32_t ps = wd.pos[i], m = wd.mask[i], ds = wd.dst[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] |= ((Wq[u] >> ps) & m) << ds;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (!((tab[wd.off + (x[u] >> 5)] >> (x[u] & 31)) & 1u)) vm &= ~(1u << u);
+  }
+  for (int i = 0; i < c->n_generic && vm; ++i) {
+    const GroupDev &G = sd.groups[sd.generic[i]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!((vm >> u) & 1u)) continue;
+      uint32_t sub = 0;
+      for (int k = 0; k < G.n; ++k) {
+        const int p = G.param[k];
+        sub += ((Wq[u] >> c->pos[p]) & ((1u << c->width[p]) - 1u)) * G.sub_stride[k];
+      }
+      if (!((__ldg(sd.table + G.off_words + (sub >> 5)) >> (sub & 31)) & 1u)) vm &= ~(1u << u);
+    }
+  }
+  return vm;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_incl(T v) {
   const int lane = threadIdx.x & 31;
@@ -296,9 +386,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr int kBWarps = THREADS / 32;
   constexpr int kTopkBytes = kBWarps * KTUNE_MAX_K * 16;   // per-warp lists (key + raw)
   __shared__ float red_mn[kBWarps], red_mx[kBWarps];
-  __shared__ uint32_t shc[32];
-  __shared__ int sh_count;
-  __shared__ uint32_t sh_tile_prefix;
   __shared__ int sh_active[KTUNE_MAX_COUNTERS];
   __shared__ int sh_nact;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -331,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int tree_bytes = pack_tree_bytes(D, narrow);
     constexpr bool topk = TOPK;
     const int k = st.k;
-    int budget = kSmemBudget - (topk ? kTopkBytes : 0) - (MODE == 2 ? kOtfBytes : 0);
+    int budget = kBScoreSmem - (topk ? kTopkBytes : 0) - (MODE == 2 ? kOtfBytes + kCtxMax : 0);
     const int per_group = max(1, budget / tree_bytes);
     const int n_groups = max(1, (n_active + per_group - 1) / per_group);
     uint8_t *tk_base = smem + (size_t)per_group * tree_bytes;
@@ -341,6 +428,34 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t *ol_w = reinterpret_cast<uint32_t *>(otf_base);
     uint32_t *ol_ord = ol_w + kOtfCap;
     uint32_t *ol_raw = ol_ord + kOtfCap;
+    OtfCtx *ctx = reinterpret_cast<OtfCtx *>(smem + kBScoreSmem - kCtxMax);
+    if constexpr (MODE == 2) {
+      // the previous item's walks are done (barrier at the top of the item loop)
+      if (threadIdx.x < KTUNE_MAX_PARAMS) {
+        const int j = threadIdx.x;
+        ctx->pos[j] = sd.pos[j];
+        ctx->width[j] = sd.width[j];
+        ctx->radix[j] = (uint8_t)sd.sa.radix[j];
+        ctx->inc[j] = sd.inc128[j];
+      }
+      for (int i = threadIdx.x; i < (int)(sizeof(ctx->win) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t *>(ctx->win)[i] = reinterpret_cast<const uint32_t *>(sd.win)[i];
+      if (threadIdx.x == 0) {
+        int top = sd.sa.P;
+        for (int j = 0; j < sd.sa.P; ++j)
+          if (sd.inc128[j]) {
+            top = j;
+            break;
+          }
+        ctx->P = sd.sa.P;
+        ctx->n_win = sd.n_win;
+        ctx->n_generic = sd.n_generic;
+        ctx->inc_top = top;
+      }
+      uint32_t *tab = reinterpret_cast<uint32_t *>(ctx + 1);
+      for (int i = threadIdx.x; i < sd.win_words; i += blockDim.x) tab[i] = __ldg(sd.win_table + i);
+      __syncthreads();
+    }
     if (topk) {
       for (int e = lane; e < KTUNE_MAX_K; e += 32) {
         tk_key[e] = 0;
@@ -459,107 +574,106 @@ __global__ void __launch_bounds__(THREADS, 1)
           walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in);
         }
       } else {
-        // on-the-fly: decode raw tiles into the list, walk it in batches of
-        // kBThreads * CPT configurations.  A decode round covers half a raw
-        // tile (kRound = 2048 of kEnumTileRaw = 4096), so rounds never straddle
-        // tiles; a valid index's ordinal is the tile's valid prefix plus its
-        // rank among the tile's valid indices.
-        if (threadIdx.x == 0) sh_count = 0;
-        __syncthreads();
-        constexpr int kRound = kBThreads * kOtfRun;
-        static_assert(kEnumTileRaw % kRound == 0, "rounds must tile the raw tiles");
-        const int64_t rlo = it.lo * kEnumTileRaw;
-        const int64_t rhi = it.hi * kEnumTileRaw < sd.sa.n_raw ? it.hi * kEnumTileRaw : sd.sa.n_raw;
-        for (int64_t r0 = rlo; r0 < rhi || sh_count > 0;) {
-          if (r0 < rhi && sh_count <= kOtfCap - kRound) {
-            if (threadIdx.x == 0 && (r0 % kEnumTileRaw) == 0) sh_tile_prefix = 0;
-            const int64_t rr = r0 + (int64_t)threadIdx.x * kOtfRun;
-            uint32_t vm = 0, W0 = 0;
-            if (rr < rhi) {
-              uint32_t W = decode_word(sd, (uint32_t)rr);
-              W0 = W;
-              const int64_t left = rhi - rr;
-              const int n = left < kOtfRun ? (int)left : kOtfRun;
-              for (int q = 0; q < n; ++q) {
-                if (valid_word(sd, W)) vm |= 1u << q;
-                W = next_word(sd, W);
+        // on-the-fly: every warp decodes whole raw tiles by itself.  Lane l
+        // takes raw indices base + 4 l .. base + 4 l + 3 of each round of 128,
+        // checks them against the window tables, and the valid unevaluated
+        // ones go to the warp's own list, which is walked CPT entries per lane
+        // at a time.  A valid index's ordinal is its tile's valid prefix plus
+        // its rank within the tile, counted round by round with warp scans.
+        constexpr int kWarpCap = kOtfCap / kBWarps;
+        constexpr int kBatchE = 32 * CPT;
+        static_assert(kWarpCap >= kBatchE + 128, "a warp list holds one batch plus one round");
+        uint32_t *lw = ol_w + warp * kWarpCap;
+        uint32_t *lo_ord = ol_ord + warp * kWarpCap;
+        uint32_t *lr = ol_raw + warp * kWarpCap;
+        int lcount = 0;
+        const uint32_t n_raw = (uint32_t)sd.sa.n_raw;
+        const int64_t eval_words = (sd.N + 31) >> 5;
+        auto walk_list = [&](int take) {
+          uint32_t Wv[CPT];
+          uint64_t Pv[CPT];
+          float s_in[CPT];
+          int64_t ordv[CPT], rawv[CPT];
+          bool ok[CPT];
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) {
+            const int e = c * 32 + lane;
+            ok[c] = e < take;
+            Wv[c] = ok[c] ? lw[e] : 0u;
+            ordv[c] = ok[c] ? (int64_t)lo_ord[e] : 0;
+            rawv[c] = ok[c] ? (int64_t)lr[e] : 0;
+            Pv[c] = 0;
+            s_in[c] = (first || !ok[c]) ? 0.0f : s_p[ordv[c]];
+          }
+          __syncwarp();
+          const int rem = lcount - take;   // < take: source and destination do not overlap
+          for (int e = lane; e < rem; e += 32) {
+            lw[e] = lw[take + e];
+            lo_ord[e] = lo_ord[take + e];
+            lr[e] = lr[take + e];
+          }
+          __syncwarp();
+          lcount = rem;
+          walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in);
+        };
+        for (int64_t t = it.lo + warp; t < it.hi; t += kBWarps) {
+          const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
+          int64_t ord_base = __ldg(sd.tile_offset + t);
+          uint32_t W = otf_decode(ctx, tbase + 4u * (uint32_t)lane);
+          for (int q = 0; q < kEnumTileRaw / 128; ++q) {
+            const uint32_t rb = tbase + (uint32_t)q * 128u;
+            if (rb >= n_raw) break;                       // warp-uniform
+            const uint32_t r0 = rb + 4u * (uint32_t)lane;
+            uint32_t Wq[4];
+            Wq[0] = W;
+#pragma unroll
+            for (int u = 1; u < 4; ++u) Wq[u] = otf_next(ctx, Wq[u - 1]);
+            const int n_here = r0 >= n_raw ? 0 : (int)min(4u, n_raw - r0);
+            const uint32_t vm = otf_valid4(ctx, sd, Wq, n_here);
+            const uint32_t cnt = __popc(vm);
+            const uint32_t incl = warp_incl(cnt);
+            const uint32_t tot = __shfl_sync(FULL, incl, 31);
+            // evaluated bits of the round's ordinals [ord_base, ord_base + tot): at most 5 words
+            const int64_t wb = ord_base >> 5;
+            uint32_t ew = 0;
+            if (lane < 5 && wb + lane < eval_words) ew = __ldg(eval_p + wb + lane);
+            uint32_t keep = 0, slot = incl - cnt;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int64_t rel = ord_base + slot - (wb << 5);
+              const uint32_t word = __shfl_sync(FULL, ew, (int)((rel >> 5) & 7));
+              if ((vm >> u) & 1u) {
+                if (!((word >> (rel & 31)) & 1u)) keep |= 1u << u;
+                ++slot;
               }
             }
-            const uint32_t cv = __popc(vm);
-            uint32_t tot;
-            const uint32_t incl = block_incl<uint32_t>(cv, shc, &tot);
-            const int64_t ord_base = __ldg(sd.tile_offset + r0 / kEnumTileRaw) +
-                                     (int64_t)sh_tile_prefix + (int64_t)(incl - cv);
-            uint32_t keep = 0;
+            const uint32_t kc = __popc(keep);
+            const uint32_t kincl = warp_incl(kc);
+            const uint32_t ktot = __shfl_sync(FULL, kincl, 31);
             {
-              int slot = 0;
-              for (int q = 0; q < kOtfRun; ++q)
-                if ((vm >> q) & 1u) {
-                  if (!is_ev(sd.eval, ord_base + slot)) keep |= 1u << q;
-                  ++slot;
-                }
-            }
-            const uint32_t ck = __popc(keep);
-            uint32_t tot2;
-            const uint32_t incl2 = block_incl<uint32_t>(ck, shc, &tot2);
-            int pos = sh_count + (int)(incl2 - ck);
-            {
-              uint32_t W = W0;
-              int slot = 0;
-              for (int q = 0; q < kOtfRun; ++q) {
-                if ((vm >> q) & 1u) {
-                  if ((keep >> q) & 1u) {
-                    ol_w[pos] = W;
-                    ol_ord[pos] = (uint32_t)(ord_base + slot);
-                    ol_raw[pos] = (uint32_t)(rr + q);
+              int pos = lcount + (int)(kincl - kc);
+              uint32_t sl = incl - cnt;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if ((vm >> u) & 1u) {
+                  if ((keep >> u) & 1u) {
+                    lw[pos] = Wq[u];
+                    lo_ord[pos] = (uint32_t)(ord_base + sl);
+                    lr[pos] = r0 + u;
                     ++pos;
                   }
-                  ++slot;
+                  ++sl;
                 }
-                W = next_word(sd, W);
               }
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-              sh_count += (int)tot2;
-              sh_tile_prefix += tot;
-            }
-            __syncthreads();
-            r0 += kRound;
-          }
-          const int cnt = sh_count;
-          if (cnt >= kBThreads * CPT || (r0 >= rhi && cnt > 0)) {
-            const int take = min(cnt, kBThreads * CPT);
-            uint32_t Wv[CPT];
-            uint64_t Pv[CPT];
-            float s_in[CPT];
-            int64_t ordv[CPT], rawv[CPT];
-            bool ok[CPT];
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-              const int e = c * kBThreads + threadIdx.x;
-              ok[c] = e < take;
-              Wv[c] = ok[c] ? ol_w[e] : 0u;
-              ordv[c] = ok[c] ? (int64_t)ol_ord[e] : 0;
-              rawv[c] = ok[c] ? (int64_t)ol_raw[e] : 0;
-              Pv[c] = 0;
-              s_in[c] = (first || !ok[c]) ? 0.0f : s_p[ordv[c]];
-            }
-            __syncthreads();
-            // move the remainder to the front
-            const int rem = cnt - take;
-            for (int e = threadIdx.x; e < rem; e += blockDim.x) {
-              const uint32_t a = ol_w[take + e], b = ol_ord[take + e], c2 = ol_raw[take + e];
-              ol_w[e] = a;
-              ol_ord[e] = b;
-              ol_raw[e] = c2;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) sh_count = rem;
-            walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in);
-            __syncthreads();
+            __syncwarp();
+            lcount += (int)ktot;
+            ord_base += tot;
+            if (lcount >= kBatchE) walk_list(kBatchE);
+            W = otf_add128(ctx, W);
           }
         }
+        if (lcount > 0) walk_list(lcount);
       }
     }
     // item epilogue: per-search min / max, top-k candidates
@@ -969,10 +1083,10 @@ static void launch_one(const SearchDev *srch, const StepDev *steps, const ItemDe
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_bscore<THREADS, CPT, MODE, TOPK>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kBScoreSmem);
     attr = true;
   }
-  k_bscore<THREADS, CPT, MODE, TOPK><<<grid, THREADS, kSmemBudget, st>>>(srch, steps, items, n_items);
+  k_bscore<THREADS, CPT, MODE, TOPK><<<grid, THREADS, kBScoreSmem, st>>>(srch, steps, items, n_items);
 }
 
 template <int MODE, bool TOPK>
