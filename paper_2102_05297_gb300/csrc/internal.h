@@ -194,6 +194,11 @@ void launch_mark(uint32_t *evaluated, int64_t ordinal, cudaStream_t st);
 // ---- MLP counter model (k_mlp.cu) ----
 constexpr int kMlpHidden = 256;
 constexpr int kMlpMaxF = 384;           // feature columns (multiple of 16)
+// weights of the pipelined forward: chunks of kMlpChunkK K-columns in the
+// shared-memory operand layout, streamed through kMlpStages stages
+constexpr int kMlpChunkK = 32;
+constexpr int kMlpStages = 5;
+constexpr int kMlpStageBytes = kMlpHidden * kMlpChunkK * 2;
 
 // The network as the fused forward kernel reads it (all device pointers).
 struct MlpDev {
@@ -203,6 +208,8 @@ struct MlpDev {
   const float *range;       // [K] output scale per counter
   const int *off;           // [P + 1] one-hot offset per parameter; off[P] = start of the u block
   const uint16_t *utab;     // [P][16] bf16 u value per digit
+  const uint8_t *wc;        // chunked operand-layout copy of w[0..3] (pipelined forward)
+  uint32_t wc_off[4];       // byte offset of each layer's first chunk in wc
 };
 
 // Epilogue operands of the training GEMM (see k_gemm_tc).
@@ -219,6 +226,12 @@ struct EpiArgs {
 };
 
 int mlp_fwd_smem(int F);
+bool mlp_pipe_supported(int F);
+void mlp_pipe_set_attrs();
+void launch_pack_wc(const uint16_t *w, int Nl, int Kl, uint8_t *dst, cudaStream_t st);
+void launch_mlp_pipe(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
+                     const float *pcprof, const float *delta, const uint32_t *evaluated,
+                     int *minmax, int *status, int max_ctas, cudaStream_t st);
 void launch_gemm_tc(int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
                     int K, const EpiArgs &ep, int *status, cudaStream_t st);
 void launch_features(const uint64_t *packed, const int *idx, int B, int P, int F, const int *off,
@@ -400,6 +413,8 @@ struct ktune_mlp {
   // W1 256 x F, b1, W2 256 x 256, b2, W3, b3, W4 Kp x 256 (rows >= K zero), b4 [Kp]
   float *d_p[8] = {}, *d_g[8] = {}, *d_m[8] = {}, *d_v[8] = {};
   uint16_t *d_wb[4] = {}, *d_wt[4] = {};   // bf16 copies and transposes (d_wt[0] unused)
+  uint8_t *d_wc = nullptr;                 // chunked operand-layout copy of d_wb
+  uint32_t wc_off[4] = {};
   float *d_range = nullptr;
   int *d_off = nullptr;
   uint16_t *d_utab = nullptr;

@@ -484,6 +484,7 @@ void mlp_set_attrs(int F) {
   cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  mlp_pipe_set_attrs();
   if (F > 0) {
     const int smem = mlp_fwd_smem(kMlpMaxF);
     cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -540,6 +541,16 @@ void launch_to_bf16(const float *p, int rows, int cols, uint16_t *wb, uint16_t *
 void launch_mlp_fwd(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
                     const float *pcprof, const float *delta, const uint32_t *evaluated,
                     int *minmax, int *status, int grid, cudaStream_t st) {
+  if (md.wc && mlp_pipe_supported(md.F)) {
+    int sms = grid;
+    if (sms <= 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    launch_mlp_pipe(mode, md, packed, n, out, pcprof, delta, evaluated, minmax, status, sms, st);
+    return;
+  }
   const int smem = mlp_fwd_smem(md.F);
   const int64_t tiles = (n + 127) / 128;
   if (tiles == 0) return;

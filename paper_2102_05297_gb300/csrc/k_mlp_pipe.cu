@@ -1,0 +1,365 @@
+// Pipelined fused forward of the MLP counter model on Blackwell tensor cores.
+//
+// One persistent CTA per SM scores its configurations two 128-row tiles at a
+// time, with three warp roles:
+//   warp 0      streams the weights, layer by layer in chunks of 32 K-columns
+//               already laid out as the shared-memory operand, through a ring
+//               of kPipeStages stages with asynchronous bulk copies;
+//   warp 1      issues tcgen05.mma for tile x (x = 0, 1) into its own 256-column
+//               tensor-memory accumulator, one layer at a time, as soon as the
+//               layer's input activations and weight chunks are in place;
+//   warps 2..9  build the features, and drain the accumulators: bias + GELU +
+//               bfloat16 into the tile's activation buffer (the next layer's
+//               A operand), or, after the output layer, the predicted counters
+//               or the Eq. score of every configuration with the minimum and
+//               maximum over the unevaluated ones.
+// The MMAs of one tile overlap the epilogue of the other.  The arithmetic is
+// that of k_mlp_fwd (same roundings, same order within every dot product's
+// epilogue and within the score's sum over counters); only the schedule
+// differs.  Every wait is bounded: on time-out the kernel records
+// KTUNE_ETIMEOUT, drains its own copies and MMAs (bounded) and returns.
+#include <float.h>
+#include <limits.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace ktune {
+
+namespace {
+
+constexpr uint64_t kPipeWait = 1000000000ull;             // 1 s per wait
+constexpr int kActBytes = 128 * kMlpHidden * 2;           // one tile's activations (64 KB)
+constexpr int kPipeSmem = 2 * kActBytes + kMlpStages * kMlpStageBytes;
+constexpr int kPipeThreads = 320;
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float gelu_p(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ int okey_p(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+
+__device__ __forceinline__ uint4 pack8_p(const uint16_t *h) {
+  uint4 q;
+  q.x = h[0] | ((uint32_t)h[1] << 16);
+  q.y = h[2] | ((uint32_t)h[3] << 16);
+  q.z = h[4] | ((uint32_t)h[5] << 16);
+  q.w = h[6] | ((uint32_t)h[7] << 16);
+  return q;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on mbarrier b.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(tc::smem_u32(b))
+      : "memory");
+}
+
+__device__ __forceinline__ int layer_k(const MlpDev &md, int l) { return l == 0 ? md.F : kMlpHidden; }
+__device__ __forceinline__ int layer_n(const MlpDev &md, int l) { return l == 3 ? md.Kp : kMlpHidden; }
+
+template <int MODE>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    k_mlp_pipe(const MlpDev md, const uint64_t *__restrict__ packed, int64_t n,
+               float *__restrict__ out, const float *__restrict__ pcprof,
+               const float *__restrict__ delta, const uint32_t *__restrict__ evaluated,
+               int *__restrict__ minmax, int *status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t *ring = sm + 2 * kActBytes;
+  __shared__ uint64_t full[kMlpStages], empty[kMlpStages], acc_full[2], act_ready[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sh_b[3 * kMlpHidden + 64];
+  __shared__ float sh_rng[KTUNE_MAX_COUNTERS], sh_pc[KTUNE_MAX_COUNTERS], sh_dl[KTUNE_MAX_COUNTERS];
+  __shared__ int sh_off[KTUNE_MAX_PARAMS + 1];
+  __shared__ uint16_t sh_utab[KTUNE_MAX_PARAMS * 16];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_tiles = (n + 127) / 128;
+  const int64_t my_tiles =
+      (int64_t)blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t n_pairs = (my_tiles + 1) / 2;
+
+  if (warp == 1) tc::tmem_alloc(&tmem_base, 512);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kMlpStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int x = 0; x < 2; ++x) {
+      tc::mbar_init(&acc_full[x], 1);
+      tc::mbar_init(&act_ready[x], 8);
+    }
+    tc::mbar_init(&drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < 3 * kMlpHidden; i += blockDim.x) sh_b[i] = md.b[i >> 8][i & 255];
+  for (int i = threadIdx.x; i < md.Kp; i += blockDim.x) sh_b[3 * kMlpHidden + i] = md.b[3][i];
+  for (int i = threadIdx.x; i < md.K; i += blockDim.x) {
+    sh_rng[i] = md.range[i];
+    sh_pc[i] = MODE == 1 ? pcprof[i] : 0.0f;
+    sh_dl[i] = MODE == 1 ? delta[i] : 0.0f;
+  }
+  for (int i = threadIdx.x; i <= md.P; i += blockDim.x) sh_off[i] = md.off[i];
+  for (int i = threadIdx.x; i < md.P * 16; i += blockDim.x) sh_utab[i] = md.utab[i];
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---- producer: weight chunks in job order (pair, layer, tile) -------------------
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t use = 0;
+      const uint32_t ring_a = tc::smem_u32(ring);
+      for (int64_t p = 0; p < n_pairs && ok; ++p)
+        for (int l = 0; l < 4 && ok; ++l)
+          for (int x = 0; x < 2 && ok; ++x) {
+            const int Kl = layer_k(md, l), Nl = layer_n(md, l);
+            for (int k0 = 0, c = 0; k0 < Kl; k0 += kMlpChunkK, ++c) {
+              const int kc = min(kMlpChunkK, Kl - k0);
+              const uint32_t st = use % kMlpStages;
+              if (use >= (uint32_t)kMlpStages &&
+                  !tc::mbar_wait(&empty[st], ((use / kMlpStages) - 1u) & 1u, kPipeWait)) {
+                ok = false;
+                break;
+              }
+              const uint32_t bytes = (uint32_t)(Nl * kc * 2);
+              mbar_expect_tx(&full[st], bytes);
+              bulk_g2s(ring_a + st * (uint32_t)kMlpStageBytes,
+                       md.wc + md.wc_off[l] + (size_t)c * Nl * kMlpChunkK * 2, bytes, &full[st]);
+              ++use;
+            }
+          }
+      if (!ok) atomicExch(status, KTUNE_ETIMEOUT);
+      // copies still in flight land before the CTA leaves (done already unless a wait gave up)
+      for (uint32_t u = use > (uint32_t)kMlpStages ? use - kMlpStages : 0u; u < use; ++u)
+        tc::mbar_wait(&full[u % kMlpStages], (u / kMlpStages) & 1u, kPipeWait);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ---------------------------------------------------------------
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t use = 0, aph[2] = {0u, 0u};
+      const uint32_t act_a = tc::smem_u32(sm), ring_a = tc::smem_u32(ring);
+      for (int64_t p = 0; p < n_pairs && ok; ++p)
+        for (int l = 0; l < 4 && ok; ++l)
+          for (int x = 0; x < 2 && ok; ++x) {
+            if (!tc::mbar_wait(&act_ready[x], aph[x], kPipeWait)) {
+              ok = false;
+              break;
+            }
+            aph[x] ^= 1u;
+            tc::fence_after();
+            const int Kl = layer_k(md, l), Nl = layer_n(md, l);
+            const uint32_t idesc = tc::idesc_bf16(128, Nl);
+            const uint32_t a0 = act_a + (uint32_t)x * kActBytes;
+            const uint32_t d = tmem + (uint32_t)x * 256u;
+            for (int k0 = 0; k0 < Kl; k0 += kMlpChunkK) {
+              const int kc = min(kMlpChunkK, Kl - k0);
+              const uint32_t st = use % kMlpStages;
+              if (!tc::mbar_wait(&full[st], (use / kMlpStages) & 1u, kPipeWait)) {
+                ok = false;
+                break;
+              }
+              tc::fence_after();
+              const uint32_t b0 = ring_a + st * (uint32_t)kMlpStageBytes;
+              for (int q = 0; q < kc / 16; ++q) {
+                const uint64_t ad =
+                    tc::sdesc(a0 + (uint32_t)((k0 + q * 16) >> 3) * 128u, 128, (uint32_t)Kl * 16u);
+                const uint64_t bd = tc::sdesc(b0 + (uint32_t)q * 256u, 128, (uint32_t)kc * 16u);
+                tc::mma_bf16(d, ad, bd, idesc, (k0 > 0 || q > 0) ? 1u : 0u);
+              }
+              tc::mma_commit(&empty[st]);
+              ++use;
+            }
+            if (!ok) break;
+            tc::mma_commit(&acc_full[x]);
+          }
+      if (!ok) atomicExch(status, KTUNE_ETIMEOUT);
+      // every MMA issued has completed before tensor memory is released
+      tc::mma_commit(&drain);
+      tc::mbar_wait(&drain, 0u, kPipeWait);
+    }
+  } else {
+    // ---- epilogue warps -----------------------------------------------------------
+    const int ew = warp - 2;
+    const int quarter = warp & 3;             // tensor-memory lanes this warp may read
+    const int half = ew >> 2;                 // hidden columns [128 half, 128 half + 128)
+    const int row = quarter * 32 + lane;      // row of the tile
+    const int F = md.F;
+    bool ok = true;
+    uint32_t aph[2] = {0u, 0u};
+    float s_mn = INFINITY, s_mx = -INFINITY;
+    auto tile_of = [&](int64_t p, int x) -> int64_t {
+      const int64_t j = 2 * p + x;
+      return j < my_tiles ? (int64_t)blockIdx.x + j * (int64_t)gridDim.x : -1;
+    };
+    // features of configuration (tile, row) into tile slot x, then arrive
+    auto build = [&](int x, int64_t tile) {
+      if (half == 0) {
+        uint8_t *X = sm + x * kActBytes;
+        const int64_t i = tile >= 0 ? tile * 128 + row : -1;
+        const uint4 zero = make_uint4(0, 0, 0, 0);
+        for (int c0 = 0; c0 < F; c0 += 8) *reinterpret_cast<uint4 *>(X + tc::core_off(row, c0, F)) = zero;
+        if (i >= 0 && i < n) {
+          const uint64_t pk = packed[i];
+          for (int j = 0; j < md.P; ++j) {
+            const uint32_t dg = nib64(pk, j);
+            *reinterpret_cast<uint16_t *>(X + tc::core_off(row, sh_off[j] + (int)dg, F)) = 0x3F80;
+            *reinterpret_cast<uint16_t *>(X + tc::core_off(row, sh_off[md.P] + j, F)) =
+                sh_utab[j * 16 + dg];
+          }
+        }
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&act_ready[x]);
+    };
+    if (n_pairs > 0) {
+      build(0, tile_of(0, 0));
+      build(1, tile_of(0, 1));
+    }
+    for (int64_t p = 0; p < n_pairs && ok; ++p)
+      for (int l = 0; l < 4 && ok; ++l)
+        for (int x = 0; x < 2; ++x) {
+          ok = __all_sync(FULL, tc::mbar_wait(&acc_full[x], aph[x], kPipeWait));
+          if (!ok) break;
+          aph[x] ^= 1u;
+          tc::fence_after();
+          const int64_t tile = tile_of(p, x);
+          const uint32_t tacc = tmem + (uint32_t)x * 256u + ((uint32_t)(quarter * 32) << 16);
+          if (l < 3) {
+            uint8_t *H = sm + x * kActBytes;
+            const float *bias = sh_b + l * kMlpHidden;
+            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+              float v[16];
+              tc::tmem_ld16(tacc + c0, v);
+              uint16_t h[16];
+#pragma unroll
+              for (int e = 0; e < 16; ++e) h[e] = tc::f2bf(gelu_p(__fadd_rn(v[e], bias[c0 + e])));
+              *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0, kMlpHidden)) = pack8_p(h);
+              *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0 + 8, kMlpHidden)) = pack8_p(h + 8);
+            }
+            tc::fence_async_smem();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&act_ready[x]);
+          } else {
+            if (half == 0) {
+              const int64_t i = tile >= 0 ? tile * 128 + row : -1;
+              const bool valid = i >= 0 && i < n;
+              const float *b4 = sh_b + 3 * kMlpHidden;
+              float s = 0.0f;
+              for (int c0 = 0; c0 < md.Kp; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tacc + c0, v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  const int c = c0 + e;
+                  if (c >= md.K) continue;
+                  const float a = __fmul_rn(__fadd_rn(v[e], b4[c]), sh_rng[c]);
+                  if (MODE == 0) {
+                    if (valid) out[(size_t)i * md.K + c] = a;
+                  } else {
+                    const float A = sh_pc[c], dl = sh_dl[c];
+                    const float den = __fadd_rn(a, A);
+                    float t = 0.0f;
+                    if (dl != 0.0f && A != 0.0f && a != 0.0f && den != 0.0f)
+                      t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(a, A), den));
+                    s = __fadd_rn(s, t);
+                  }
+                }
+              }
+              if (MODE == 1 && valid) {
+                out[i] = s;
+                if (!((evaluated[i >> 5] >> (i & 31)) & 1u)) {
+                  s_mn = fminf(s_mn, s);
+                  s_mx = fmaxf(s_mx, s);
+                }
+              }
+            }
+            tc::fence_before();
+            if (p + 1 < n_pairs) build(x, tile_of(p + 1, x));
+          }
+        }
+    if (!ok) {
+      if (lane == 0) atomicExch(status, KTUNE_ETIMEOUT);
+    } else if (MODE == 1) {
+      for (int o = 16; o; o >>= 1) {
+        s_mn = fminf(s_mn, __shfl_xor_sync(FULL, s_mn, o));
+        s_mx = fmaxf(s_mx, __shfl_xor_sync(FULL, s_mx, o));
+      }
+      if (lane == 0 && s_mn <= s_mx) {
+        atomicMin(minmax, okey_p(s_mn));
+        atomicMax(minmax + 1, okey_p(s_mx));
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// Row-major bf16 weights of one layer (Nl rows, Kl columns) into the chunked
+// operand layout: chunk c holds columns [32 c, 32 c + kc) of every row as core
+// matrices with KC = kc.  One thread moves 8 consecutive columns.
+__global__ void k_pack_wc(const uint16_t *__restrict__ w, int Nl, int Kl, uint8_t *__restrict__ dst) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int per_row = Kl >> 3;
+  if (g >= (int64_t)Nl * per_row) return;
+  const int r = (int)(g / per_row), k = (int)(g - (int64_t)r * per_row) * 8;
+  const int c = k / kMlpChunkK, kk = k - c * kMlpChunkK;
+  const int kc = min(kMlpChunkK, Kl - c * kMlpChunkK);
+  const uint4 v = *reinterpret_cast<const uint4 *>(w + (size_t)r * Kl + k);
+  *reinterpret_cast<uint4 *>(dst + (size_t)c * Nl * kMlpChunkK * 2 + tc::core_off(r, kk, kc)) = v;
+}
+
+}  // namespace
+
+bool mlp_pipe_supported(int F) { return F <= kMlpHidden; }
+
+void mlp_pipe_set_attrs() {
+  cudaFuncSetAttribute(k_mlp_pipe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
+  cudaFuncSetAttribute(k_mlp_pipe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
+}
+
+void launch_pack_wc(const uint16_t *w, int Nl, int Kl, uint8_t *dst, cudaStream_t st) {
+  const int64_t n = (int64_t)Nl * (Kl >> 3);
+  k_pack_wc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, Nl, Kl, dst);
+}
+
+void launch_mlp_pipe(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
+                     const float *pcprof, const float *delta, const uint32_t *evaluated,
+                     int *minmax, int *status, int max_ctas, cudaStream_t st) {
+  const int64_t tiles = (n + 127) / 128;
+  if (tiles == 0) return;
+  const int64_t pairs = (tiles + 1) / 2;
+  int grid = (int)std::min<int64_t>(pairs, max_ctas > 0 ? max_ctas : pairs);
+  if (mode == 0)
+    k_mlp_pipe<0><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, out, pcprof, delta,
+                                                          evaluated, minmax, status);
+  else
+    k_mlp_pipe<1><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, out, pcprof, delta,
+                                                          evaluated, minmax, status);
+}
+
+}  // namespace ktune

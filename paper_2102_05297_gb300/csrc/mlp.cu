@@ -175,6 +175,12 @@ int ensure_pred(ktune_mlp *m, int64_t n) {
 
 }  // namespace
 
+// Refresh the chunked weight copy after the bf16 weights changed.
+void pack_weights(ktune_mlp *m) {
+  for (int l = 0; l < 4; ++l)
+    launch_pack_wc(m->d_wb[l], m->rows(2 * l), m->cols(2 * l), m->d_wc + m->wc_off[l], m->stream);
+}
+
 MlpDev ktune_mlp::dev() const {
   MlpDev d{};
   d.P = P;
@@ -188,6 +194,8 @@ MlpDev ktune_mlp::dev() const {
   d.range = d_range;
   d.off = d_off;
   d.utab = d_utab;
+  d.wc = d_wc;
+  for (int l = 0; l < 4; ++l) d.wc_off[l] = wc_off[l];
   return d;
 }
 
@@ -268,6 +276,15 @@ int ktune_mlp_create(ktune_space *s, int K, const int32_t *roles, const float *r
       cudaMemset(m->d_wt[l], 0, n * 2);
     }
   }
+  {  // chunked operand-layout copy of the bf16 weights (pipelined forward)
+    uint32_t off = 0;
+    for (int l = 0; l < 4; ++l) {
+      m->wc_off[l] = off;
+      off += (uint32_t)((size_t)m->rows(2 * l) * m->cols(2 * l) * 2);
+    }
+    if ((rc = dalloc(&m->d_wc, off))) return fail(rc);
+    cudaMemset(m->d_wc, 0, off);
+  }
   const size_t B = (size_t)max_batch, H = kMlpHidden;
   if ((rc = dalloc(&m->d_range, K)) || (rc = dalloc(&m->d_off, P + 1)) ||
       (rc = dalloc(&m->d_utab, utab.size())) || (rc = dalloc(&m->d_X, B * F)) ||
@@ -307,6 +324,7 @@ int ktune_mlp_destroy(ktune_mlp *m) {
     cudaFree(m->d_wb[l]);
     cudaFree(m->d_wt[l]);
   }
+  cudaFree(m->d_wc);
   for (int l = 0; l < 3; ++l) {
     cudaFree(m->d_Z[l]);
     cudaFree(m->d_A[l]);
@@ -363,6 +381,7 @@ int ktune_mlp_set_params(ktune_mlp *m, const float *params) {
   for (int l = 0; l < 4; ++l)
     launch_to_bf16(m->d_p[2 * l], m->rows(2 * l), m->cols(2 * l), m->d_wb[l],
                    l > 0 ? m->d_wt[l] : nullptr, m->stream);
+  pack_weights(m);
   CK(cudaGetLastError());
   m->adam_t = 0;
   return finish(m);
@@ -471,6 +490,7 @@ int ktune_mlp_train(ktune_mlp *m, const int32_t *idx, int B, int steps, float lr
                   w ? m->d_wb[l] : nullptr, (w && l > 0) ? m->d_wt[l] : nullptr, m->stream);
     }
   }
+  pack_weights(m);
   const cudaError_t le = cudaGetLastError();
   int rc = finish(m);
   if (le != cudaSuccess && rc == KTUNE_OK) {
