@@ -8,18 +8,20 @@
 //   warp 1      issues tcgen05.mma for tile x (x = 0, 1) into its own 256-column
 //               tensor-memory accumulator, one layer at a time, as soon as the
 //               layer's input activations and weight chunks are in place;
-//   warps 2..9  build the features, and drain the accumulators: bias + GELU +
+//   warps 2..17 build the features, and drain the accumulators: bias + GELU +
 //               bfloat16 into the tile's activation buffer (the next layer's
 //               A operand), or, after the output layer, the predicted counters
 //               or the Eq. score of every configuration with the minimum and
 //               maximum over the unevaluated ones.
 // The MMAs of one tile overlap the epilogue of the other.  The arithmetic is
-// that of k_mlp_fwd (same roundings, same order within every dot product's
-// epilogue and within the score's sum over counters); only the schedule
-// differs.  Every wait is bounded: on time-out the kernel records
+// that of k_mlp_fwd (same roundings, same order within every epilogue and
+// within the score's sum over counters) except GELU, whose erf comes from a
+// published rational approximation (gelu_p) instead of erff.  Every wait is bounded: on time-out the kernel records
 // KTUNE_ETIMEOUT, drains its own copies and MMAs (bounded) and returns.
 #include <float.h>
 #include <limits.h>
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -34,11 +36,36 @@ namespace {
 constexpr uint64_t kPipeWait = 1000000000ull;             // 1 s per wait
 constexpr int kActBytes = 128 * kMlpHidden * 2;           // one tile's activations (64 KB)
 constexpr int kPipeSmem = 2 * kActBytes + kMlpStages * kMlpStageBytes;
-constexpr int kPipeThreads = 320;
+constexpr int kEpiWarps = 16;                             // 4 per tensor-memory lane quarter
+constexpr int kPipeThreads = 64 + 32 * kEpiWarps;
 constexpr unsigned FULL = 0xffffffffu;
 
+// GELU(z) = z (1 + erf(z / sqrt 2)) / 2 with erf from Abramowitz & Stegun,
+// Handbook of Mathematical Functions, formula 7.1.28 (Hastings):
+//   erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16 + e(x),  x >= 0,
+//   |e(x)| <= 3e-7.
+// The bracket's inverse 16th power is erfc(|x|), so 1 + erf(z / sqrt 2) is
+// 2 - erfc for z >= 0 and erfc itself for z < 0 (no cancellation for negative
+// z).  For z >= 16 the power overflows, erfc is 0 and GELU(z) = z exactly.
+// With float32 arithmetic the result is within 4e-7 max(|z|, 1) of the exact
+// GELU (a float64 comparison over a dense grid of [-12, 20]), far below the
+// bfloat16 rounding the activation then takes.
 __device__ __forceinline__ float gelu_p(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+  const float x = fabsf(z) * 0.70710678118654752f;
+  float p = fmaf(4.30638e-5f, x, 2.765672e-4f);
+  p = fmaf(p, x, 1.520143e-4f);
+  p = fmaf(p, x, 9.2705272e-3f);
+  p = fmaf(p, x, 4.22820123e-2f);
+  p = fmaf(p, x, 7.05230784e-2f);
+  p = fmaf(p, x, 1.0f);
+  p = p * p;
+  p = p * p;
+  p = p * p;
+  p = p * p;
+  float q;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(p));
+  const float t = z >= 0.0f ? 2.0f - q : q;
+  return 0.5f * z * t;
 }
 
 __device__ __forceinline__ int okey_p(float f) {
@@ -46,13 +73,29 @@ __device__ __forceinline__ int okey_p(float f) {
   return b >= 0 ? b : b ^ 0x7FFFFFFF;
 }
 
-__device__ __forceinline__ uint4 pack8_p(const uint16_t *h) {
-  uint4 q;
-  q.x = h[0] | ((uint32_t)h[1] << 16);
-  q.y = h[2] | ((uint32_t)h[3] << 16);
-  q.z = h[4] | ((uint32_t)h[5] << 16);
-  q.w = h[6] | ((uint32_t)h[7] << 16);
-  return q;
+
+// Round-to-nearest-even bfloat16 pair (lo in the low half), one conversion.
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&b);
+}
+
+// 32 lanes x 32 columns of FP32 accumulators in one load.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
@@ -87,7 +130,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   uint8_t *ring = sm + 2 * kActBytes;
   __shared__ uint64_t full[kMlpStages], empty[kMlpStages], acc_full[2], act_ready[2], drain;
   __shared__ uint32_t tmem_base;
-  __shared__ float sh_b[3 * kMlpHidden + 64];
+  __shared__ __align__(16) float sh_b[3 * kMlpHidden + 64];
   __shared__ float sh_rng[KTUNE_MAX_COUNTERS], sh_pc[KTUNE_MAX_COUNTERS], sh_dl[KTUNE_MAX_COUNTERS];
   __shared__ int sh_off[KTUNE_MAX_PARAMS + 1];
   __shared__ uint16_t sh_utab[KTUNE_MAX_PARAMS * 16];
@@ -105,7 +148,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     }
     for (int x = 0; x < 2; ++x) {
       tc::mbar_init(&acc_full[x], 1);
-      tc::mbar_init(&act_ready[x], 8);
+      tc::mbar_init(&act_ready[x], kEpiWarps);
     }
     tc::mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -203,7 +246,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     // ---- epilogue warps -----------------------------------------------------------
     const int ew = warp - 2;
     const int quarter = warp & 3;             // tensor-memory lanes this warp may read
-    const int half = ew >> 2;                 // hidden columns [128 half, 128 half + 128)
+    const int cg = ew >> 2;                   // hidden columns [64 cg, 64 cg + 64)
     const int row = quarter * 32 + lane;      // row of the tile
     const int F = md.F;
     bool ok = true;
@@ -215,7 +258,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     };
     // features of configuration (tile, row) into tile slot x, then arrive
     auto build = [&](int x, int64_t tile) {
-      if (half == 0) {
+      if (cg == 0) {
         uint8_t *X = sm + x * kActBytes;
         const int64_t i = tile >= 0 ? tile * 128 + row : -1;
         const uint4 zero = make_uint4(0, 0, 0, 0);
@@ -250,21 +293,27 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           if (l < 3) {
             uint8_t *H = sm + x * kActBytes;
             const float *bias = sh_b + l * kMlpHidden;
-            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-              float v[16];
-              tc::tmem_ld16(tacc + c0, v);
-              uint16_t h[16];
+            for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 32) {
+              float v[32];
+              tmem_ld32(tacc + c0, v);
 #pragma unroll
-              for (int e = 0; e < 16; ++e) h[e] = tc::f2bf(gelu_p(__fadd_rn(v[e], bias[c0 + e])));
-              *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0, kMlpHidden)) = pack8_p(h);
-              *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0 + 8, kMlpHidden)) = pack8_p(h + 8);
+              for (int e8 = 0; e8 < 32; e8 += 8) {
+                const float4 b0 = *reinterpret_cast<const float4 *>(bias + c0 + e8);
+                const float4 b1 = *reinterpret_cast<const float4 *>(bias + c0 + e8 + 4);
+                uint4 q;
+                q.x = bf2(gelu_p(__fadd_rn(v[e8 + 0], b0.x)), gelu_p(__fadd_rn(v[e8 + 1], b0.y)));
+                q.y = bf2(gelu_p(__fadd_rn(v[e8 + 2], b0.z)), gelu_p(__fadd_rn(v[e8 + 3], b0.w)));
+                q.z = bf2(gelu_p(__fadd_rn(v[e8 + 4], b1.x)), gelu_p(__fadd_rn(v[e8 + 5], b1.y)));
+                q.w = bf2(gelu_p(__fadd_rn(v[e8 + 6], b1.z)), gelu_p(__fadd_rn(v[e8 + 7], b1.w)));
+                *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0 + e8, kMlpHidden)) = q;
+              }
             }
             tc::fence_async_smem();
             tc::fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&act_ready[x]);
           } else {
-            if (half == 0) {
+            if (cg == 0) {
               const int64_t i = tile >= 0 ? tile * 128 + row : -1;
               const bool valid = i >= 0 && i < n;
               const float *b4 = sh_b + 3 * kMlpHidden;
