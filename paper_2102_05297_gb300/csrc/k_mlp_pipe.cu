@@ -4,20 +4,22 @@
 // time, with three warp roles:
 //   warp 0      streams the weights, layer by layer in chunks of 32 K-columns
 //               already laid out as the shared-memory operand, through a ring
-//               of kPipeStages stages with asynchronous bulk copies;
+//               of kMlpStages stages with asynchronous bulk copies;
 //   warp 1      issues tcgen05.mma for tile x (x = 0, 1) into its own 256-column
 //               tensor-memory accumulator, one layer at a time, as soon as the
 //               layer's input activations and weight chunks are in place;
-//   warps 2..17 build the features, and drain the accumulators: bias + GELU +
-//               bfloat16 into the tile's activation buffer (the next layer's
-//               A operand), or, after the output layer, the predicted counters
-//               or the Eq. score of every configuration with the minimum and
-//               maximum over the unevaluated ones.
+//   warps 2..17 two groups of eight, group x for tile x: build the features
+//               and drain the accumulator -- bias + GELU + bfloat16 into the
+//               tile's activation buffer (the next layer's A operand), or,
+//               after the output layer, the predicted counters or the Eq.
+//               score of every configuration with the minimum and maximum
+//               over the unevaluated ones.
 // The MMAs of one tile overlap the epilogue of the other.  The arithmetic is
 // that of k_mlp_fwd (same roundings, same order within every epilogue and
 // within the score's sum over counters) except GELU, whose erf comes from a
-// published rational approximation (gelu_p) instead of erff.  Every wait is bounded: on time-out the kernel records
-// KTUNE_ETIMEOUT, drains its own copies and MMAs (bounded) and returns.
+// published rational approximation (gelu_p) instead of erff.  Every wait is
+// bounded: on time-out the kernel records KTUNE_ETIMEOUT, drains its own
+// copies and MMAs (bounded) and returns.
 #include <float.h>
 #include <limits.h>
 
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     }
     for (int x = 0; x < 2; ++x) {
       tc::mbar_init(&acc_full[x], 1);
-      tc::mbar_init(&act_ready[x], kEpiWarps);
+      tc::mbar_init(&act_ready[x], kEpiWarps / 2);
     }
     tc::mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -243,28 +245,32 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       tc::mbar_wait(&drain, 0u, kPipeWait);
     }
   } else {
-    // ---- epilogue warps -----------------------------------------------------------
+    // ---- epilogue: two groups of eight warps, group x drains tile slot x --------------
     const int ew = warp - 2;
+    const int x = ew >> 3;                    // tile slot of this warp's group
     const int quarter = warp & 3;             // tensor-memory lanes this warp may read
-    const int cg = ew >> 2;                   // hidden columns [64 cg, 64 cg + 64)
+    const int cg = (ew >> 2) & 1;             // hidden columns [128 cg, 128 cg + 128)
     const int row = quarter * 32 + lane;      // row of the tile
     const int F = md.F;
     bool ok = true;
-    uint32_t aph[2] = {0u, 0u};
+    uint32_t aph = 0u;
     float s_mn = INFINITY, s_mx = -INFINITY;
-    auto tile_of = [&](int64_t p, int x) -> int64_t {
+    auto tile_of = [&](int64_t p) -> int64_t {
       const int64_t j = 2 * p + x;
       return j < my_tiles ? (int64_t)blockIdx.x + j * (int64_t)gridDim.x : -1;
     };
-    // features of configuration (tile, row) into tile slot x, then arrive
-    auto build = [&](int x, int64_t tile) {
+    auto fetch = [&](int64_t tile) -> uint64_t {
+      const int64_t i = tile >= 0 ? tile * 128 + row : -1;
+      return (cg == 0 && i >= 0 && i < n) ? packed[i] : 0ull;
+    };
+    // features of configuration (tile, row) into slot x (digits pk), then arrive
+    auto build = [&](int64_t tile, uint64_t pk) {
       if (cg == 0) {
         uint8_t *X = sm + x * kActBytes;
         const int64_t i = tile >= 0 ? tile * 128 + row : -1;
         const uint4 zero = make_uint4(0, 0, 0, 0);
         for (int c0 = 0; c0 < F; c0 += 8) *reinterpret_cast<uint4 *>(X + tc::core_off(row, c0, F)) = zero;
         if (i >= 0 && i < n) {
-          const uint64_t pk = packed[i];
           for (int j = 0; j < md.P; ++j) {
             const uint32_t dg = nib64(pk, j);
             *reinterpret_cast<uint16_t *>(X + tc::core_off(row, sh_off[j] + (int)dg, F)) = 0x3F80;
@@ -277,79 +283,77 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&act_ready[x]);
     };
-    if (n_pairs > 0) {
-      build(0, tile_of(0, 0));
-      build(1, tile_of(0, 1));
-    }
+    if (n_pairs > 0) build(tile_of(0), fetch(tile_of(0)));
     for (int64_t p = 0; p < n_pairs && ok; ++p)
-      for (int l = 0; l < 4 && ok; ++l)
-        for (int x = 0; x < 2; ++x) {
-          ok = __all_sync(FULL, tc::mbar_wait(&acc_full[x], aph[x], kPipeWait));
-          if (!ok) break;
-          aph[x] ^= 1u;
-          tc::fence_after();
-          const int64_t tile = tile_of(p, x);
-          const uint32_t tacc = tmem + (uint32_t)x * 256u + ((uint32_t)(quarter * 32) << 16);
-          if (l < 3) {
-            uint8_t *H = sm + x * kActBytes;
-            const float *bias = sh_b + l * kMlpHidden;
-            for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 32) {
-              float v[32];
-              tmem_ld32(tacc + c0, v);
+      for (int l = 0; l < 4; ++l) {
+        ok = __all_sync(FULL, tc::mbar_wait(&acc_full[x], aph, kPipeWait));
+        if (!ok) break;
+        aph ^= 1u;
+        tc::fence_after();
+        const int64_t tile = tile_of(p);
+        const uint32_t tacc = tmem + (uint32_t)x * 256u + ((uint32_t)(quarter * 32) << 16);
+        if (l < 3) {
+          uint8_t *H = sm + x * kActBytes;
+          const float *bias = sh_b + l * kMlpHidden;
+          for (int c0 = cg * 128; c0 < cg * 128 + 128; c0 += 32) {
+            float v[32];
+            tmem_ld32(tacc + c0, v);
 #pragma unroll
-              for (int e8 = 0; e8 < 32; e8 += 8) {
-                const float4 b0 = *reinterpret_cast<const float4 *>(bias + c0 + e8);
-                const float4 b1 = *reinterpret_cast<const float4 *>(bias + c0 + e8 + 4);
-                uint4 q;
-                q.x = bf2(gelu_p(__fadd_rn(v[e8 + 0], b0.x)), gelu_p(__fadd_rn(v[e8 + 1], b0.y)));
-                q.y = bf2(gelu_p(__fadd_rn(v[e8 + 2], b0.z)), gelu_p(__fadd_rn(v[e8 + 3], b0.w)));
-                q.z = bf2(gelu_p(__fadd_rn(v[e8 + 4], b1.x)), gelu_p(__fadd_rn(v[e8 + 5], b1.y)));
-                q.w = bf2(gelu_p(__fadd_rn(v[e8 + 6], b1.z)), gelu_p(__fadd_rn(v[e8 + 7], b1.w)));
-                *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0 + e8, kMlpHidden)) = q;
-              }
+            for (int e8 = 0; e8 < 32; e8 += 8) {
+              const float4 b0 = *reinterpret_cast<const float4 *>(bias + c0 + e8);
+              const float4 b1 = *reinterpret_cast<const float4 *>(bias + c0 + e8 + 4);
+              uint4 q;
+              q.x = bf2(gelu_p(__fadd_rn(v[e8 + 0], b0.x)), gelu_p(__fadd_rn(v[e8 + 1], b0.y)));
+              q.y = bf2(gelu_p(__fadd_rn(v[e8 + 2], b0.z)), gelu_p(__fadd_rn(v[e8 + 3], b0.w)));
+              q.z = bf2(gelu_p(__fadd_rn(v[e8 + 4], b1.x)), gelu_p(__fadd_rn(v[e8 + 5], b1.y)));
+              q.w = bf2(gelu_p(__fadd_rn(v[e8 + 6], b1.z)), gelu_p(__fadd_rn(v[e8 + 7], b1.w)));
+              *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0 + e8, kMlpHidden)) = q;
             }
-            tc::fence_async_smem();
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&act_ready[x]);
-          } else {
-            if (cg == 0) {
-              const int64_t i = tile >= 0 ? tile * 128 + row : -1;
-              const bool valid = i >= 0 && i < n;
-              const float *b4 = sh_b + 3 * kMlpHidden;
-              float s = 0.0f;
-              for (int c0 = 0; c0 < md.Kp; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tacc + c0, v);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                  const int c = c0 + e;
-                  if (c >= md.K) continue;
-                  const float a = __fmul_rn(__fadd_rn(v[e], b4[c]), sh_rng[c]);
-                  if (MODE == 0) {
-                    if (valid) out[(size_t)i * md.K + c] = a;
-                  } else {
-                    const float A = sh_pc[c], dl = sh_dl[c];
-                    const float den = __fadd_rn(a, A);
-                    float t = 0.0f;
-                    if (dl != 0.0f && A != 0.0f && a != 0.0f && den != 0.0f)
-                      t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(a, A), den));
-                    s = __fadd_rn(s, t);
-                  }
-                }
-              }
-              if (MODE == 1 && valid) {
-                out[i] = s;
-                if (!((evaluated[i >> 5] >> (i & 31)) & 1u)) {
-                  s_mn = fminf(s_mn, s);
-                  s_mx = fmaxf(s_mx, s);
-                }
-              }
-            }
-            tc::fence_before();
-            if (p + 1 < n_pairs) build(x, tile_of(p + 1, x));
           }
+          tc::fence_async_smem();
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&act_ready[x]);
+        } else {
+          const bool more = p + 1 < n_pairs;
+          const uint64_t pk_next = more ? fetch(tile_of(p + 1)) : 0ull;   // in flight meanwhile
+          if (cg == 0) {
+            const int64_t i = tile >= 0 ? tile * 128 + row : -1;
+            const bool valid = i >= 0 && i < n;
+            const float *b4 = sh_b + 3 * kMlpHidden;
+            float s = 0.0f;
+            for (int c0 = 0; c0 < md.Kp; c0 += 16) {
+              float v[16];
+              tc::tmem_ld16(tacc + c0, v);
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const int c = c0 + e;
+                if (c >= md.K) continue;
+                const float a = __fmul_rn(__fadd_rn(v[e], b4[c]), sh_rng[c]);
+                if (MODE == 0) {
+                  if (valid) out[(size_t)i * md.K + c] = a;
+                } else {
+                  const float A = sh_pc[c], dl = sh_dl[c];
+                  const float den = __fadd_rn(a, A);
+                  float t = 0.0f;
+                  if (dl != 0.0f && A != 0.0f && a != 0.0f && den != 0.0f)
+                    t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(a, A), den));
+                  s = __fadd_rn(s, t);
+                }
+              }
+            }
+            if (MODE == 1 && valid) {
+              out[i] = s;
+              if (!((evaluated[i >> 5] >> (i & 31)) & 1u)) {
+                s_mn = fminf(s_mn, s);
+                s_mx = fmaxf(s_mx, s);
+              }
+            }
+          }
+          tc::fence_before();
+          if (more) build(tile_of(p + 1), pk_next);
         }
+      }
     if (!ok) {
       if (lane == 0) atomicExch(status, KTUNE_ETIMEOUT);
     } else if (MODE == 1) {
