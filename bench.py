@@ -446,20 +446,31 @@ BATCH_SPACES = ["batch_%d" % i for i in range(8)]
 BATCH_K = [16, 32, 40, 32, 16, 40, 32, 16]
 
 
-def path_batch(ctx, per_space=8, depth=12):
+def path_batch(ctx, per_space=8, depth=12, mlp_steps=200):
     kt, torch, stream = ctx["kt"], ctx["torch"], ctx["stream"]
     from workloads.trees import random_model
+    from paper_2102_05297_gb300 import fit
     entries = []
     keep = []
+    mlps = []
     for si, nm in enumerate(BATCH_SPACES):
         d = W.load_space(nm)
         roles = W.layout(BATCH_K[si])
-        model = random_model(d.radices, roles, depth=depth, seed=100 + si)
         gpu = SyntheticGPU(d, roles, seed=si)
         sp = kt.Space.from_desc(d)
-        m = kt.Model(sp, model)
         valid = sp.valid_raw()
         dig = sp.valid_digits()
+        if si % 2 == 0:      # even spaces: depth-12 trees
+            m = kt.Model(sp, random_model(d.radices, roles, depth=depth, seed=100 + si))
+        else:                # odd spaces: the MLP, briefly trained on a 5% profile sample
+            mlp = kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=1024, stream=stream)
+            mlp.set_params(fit.init_mlp(mlp.F, BATCH_K[si], seed=si))
+            samp = sample_indices(len(valid), 0.05, si)
+            mlp.set_data(valid[samp], add_noise(gpu.evaluate(dig[samp])[0], si, 0.02))
+            mlp.train(np.random.default_rng(si).integers(0, len(samp), size=mlp_steps * 1024)
+                      .astype(np.int32), 1024, return_losses=False)
+            mlps.append(mlp)
+            m = kt.Model.from_mlp(mlp)
         keep += [sp, m]
         for r in range(per_space):
             s = kt.Search(sp, m, k=5, seed=10 * si + r, search_id=r, stream=stream)
@@ -480,9 +491,10 @@ def path_batch(ctx, per_space=8, depth=12):
     Wu = ctx["warmup"]
     # the counters of every step are precomputed from a recording so that
     # the timed loop holds only the batched steps
-    seqs = []
+    seqs, cps = [], []
     for i in range(Wu + n_steps):
         c = counters()
+        cps.append([e[0].current() for e in entries])
         res = b.step(c, 5)
         seqs.append(c)
         for (s, gpu, valid, dig), (raw, _) in zip(entries, res):
@@ -515,16 +527,43 @@ def path_batch(ctx, per_space=8, depth=12):
     b.close()
     for s in entries2:
         s.close()
+    # the same searches stepped one at a time (one graph launch per search step)
+    singles = []
+    for si, nm in enumerate(BATCH_SPACES):
+        sp, m = keep[2 * si], keep[2 * si + 1]
+        for r in range(per_space):
+            singles.append(kt.Search(sp, m, k=5, seed=10 * si + r, search_id=r, stream=stream))
+    ob = (torch.empty(5, dtype=torch.int64, device="cuda"),
+          torch.empty(5, dtype=torch.float32, device="cuda"),
+          torch.empty(1, dtype=torch.int32, device="cuda"))
+    t1_ms = 0.0
+    for i in range(Wu + n_steps):
+        for q, s1 in enumerate(singles):   # the c_profiles of the recorded trajectory
+            s1.set_profile(cps[i][q])
+        e0.record(stream)
+        for q, s1 in enumerate(singles):
+            s1.step_device(seqs[i][q], 5, ob[0].data_ptr(), ob[1].data_ptr(), ob[2].data_ptr(),
+                           stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= Wu:
+            t1_ms += e0.elapsed_time(e1)
+    for s1 in singles:
+        s1.close()
     thr, cpt, ipc = kt.Batch.variant(choice)
     t = t_ms / 1e3
     return {
         "workload": "%d searches (%d per space) over %d spaces of %s valid configurations, "
-                    "K %s, depth-%d random trees, k=5 weighted draws; one CUDA-graph launch per "
-                    "batched step" % (len(entries), per_space, len(BATCH_SPACES),
-                                      "/".join(str(v) for v in n_valid),
-                                      "/".join(str(k) for k in BATCH_K), depth),
+                    "K %s; even spaces scored by depth-%d random trees, odd spaces by the BF16 "
+                    "MLP (%d Adam steps x 1024 rows on a 5%% sample); k=5 weighted draws; one "
+                    "CUDA-graph launch per batched step" % (
+                        len(entries), per_space, len(BATCH_SPACES),
+                        "/".join(str(v) for v in n_valid), "/".join(str(k) for k in BATCH_K),
+                        depth, mlp_steps),
         "value": scored / t, "unit": "configs/s", "ms_per_batch_step": t_ms / n_steps,
         "search_steps_per_s": len(entries) * n_steps / t, "steps": n_steps,
+        "one_at_a_time_ms_per_batch_step": t1_ms / n_steps,
+        "speedup_vs_one_at_a_time": t1_ms / t_ms,
         "autotune": {"choice": choice, "threads": thr, "configs_per_thread": cpt,
                      "items_per_cta": ipc, "candidates_ms": [float(x) for x in ms]},
         "timing": "CUDA events around ktune_batch_step, including its device-to-host copy of "

@@ -220,6 +220,21 @@ int ktune_report(ktune_search *search, const double *runtimes, int n);
 /* Number of configurations evaluated so far (including the initial one). */
 int ktune_search_evaluated(const ktune_search *search, int64_t *n);
 
+/* Checkpoints of a search (Algorithm 1's state between steps): the options,
+ * the current c_profile, the step counter (the Philox counter word of the
+ * draws), the evaluated set and the last batch awaiting ktune_report.
+ * save: with buf NULL, *bytes receives the size needed; otherwise buf
+ * (HOST, *bytes long) receives the checkpoint and *bytes its size
+ * (KTUNE_EINVAL if too small).  Waits for the search's enqueued steps.
+ * load: creates a search over (space, model) in that state; the checkpoint
+ * must come from the same space (checked by size and a hash of its value
+ * lists and constraint tables; KTUNE_EINVAL) and a model of the same kind, K
+ * and depth (KTUNE_EMODEL).  A loaded search continues exactly as the saved
+ * one would have: the same draws, the same selections. */
+int ktune_search_save(const ktune_search *search, void *buf, size_t *bytes);
+int ktune_search_load(ktune_space *space, ktune_model *model, const void *buf, size_t bytes,
+                      void *stream, ktune_search **out);
+
 /* Statistics of the most recent step.  kernel_ms holds the device time of
  * each kernel of that step in launch order (prepare, score, weights, select),
  * measured with CUDA events on the step's stream, only while timing is

@@ -817,6 +817,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
     }
   }
   sd.nodes = m->d_nodes;
+  sd.kind = m->kind;
   sd.leaves = m->d_leaves;
   sd.K = m->K;
   sd.D = m->D;
@@ -1073,6 +1074,125 @@ int ktune_step_device(ktune_search *h, const float *counters, int k, int64_t *ou
   return KTUNE_OK;
 }
 
+// ---- checkpoints -------------------------------------------------------------
+// Blob (little-endian): header, then the last returned batch (raw indices,
+// packed digits) awaiting ktune_report, then the evaluated bitset words.
+namespace {
+constexpr uint32_t kCkptMagic = 0x4B50434Bu;   // "KCPK"
+constexpr uint32_t kCkptVersion = 1;
+struct CkptHeader {
+  uint32_t magic, version;
+  int64_t n_valid, n_raw;
+  int32_t n_params, K, depth, kind;
+  ktune_search_opts opts;
+  int64_t cprof_raw;
+  int64_t n_evaluated;
+  uint32_t step_no;
+  int32_t n_last;
+  uint64_t space_hash;      // FNV-1a over the radices and the constraint table
+};
+
+uint64_t space_hash(const ktune_space *s) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void *p, size_t n) {
+    const uint8_t *b = static_cast<const uint8_t *>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(s->sa.radix, sizeof(int) * s->sa.P);
+  mix(s->values.data(), s->values.size() * sizeof(int64_t));
+  mix(s->table.data(), s->table.size() * sizeof(uint32_t));
+  return h;
+}
+
+size_t ckpt_bytes(const ktune_search *h, size_t n_last) {
+  return sizeof(CkptHeader) + n_last * 16 + (size_t)((h->space->n_valid + 31) / 32) * 4;
+}
+}  // namespace
+
+int ktune_search_save(const ktune_search *h, void *buf, size_t *bytes) {
+  if (!h || !bytes) FAIL(KTUNE_EINVAL, "null argument");
+  const size_t need = ckpt_bytes(h, h->last_raw.size());
+  if (!buf) {
+    *bytes = need;
+    return KTUNE_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    FAIL(KTUNE_EINVAL, "checkpoint buffer too small");
+  }
+  CkptHeader hd{};
+  hd.magic = kCkptMagic;
+  hd.version = kCkptVersion;
+  hd.n_valid = h->space->n_valid;
+  hd.n_raw = h->space->sa.n_raw;
+  hd.n_params = h->space->sa.P;
+  hd.K = h->model->K;
+  hd.depth = h->model->D;
+  hd.kind = h->model->kind;
+  hd.opts = h->opts;
+  hd.cprof_raw = h->cprof_raw;
+  hd.n_evaluated = h->n_evaluated;
+  hd.step_no = h->step_no;
+  hd.n_last = (int32_t)h->last_raw.size();
+  hd.space_hash = space_hash(h->space);
+  uint8_t *p = static_cast<uint8_t *>(buf);
+  memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  if (hd.n_last) {
+    memcpy(p, h->last_raw.data(), (size_t)hd.n_last * 8);
+    memcpy(p + (size_t)hd.n_last * 8, h->last_packed.data(), (size_t)hd.n_last * 8);
+  }
+  p += (size_t)hd.n_last * 16;
+  const size_t words = (size_t)((h->space->n_valid + 31) / 32);
+  // the state includes every step enqueued so far
+  CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : h->stream));
+  CK(cudaMemcpy(p, h->d_eval, words * 4, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return KTUNE_OK;
+}
+
+int ktune_search_load(ktune_space *s, ktune_model *m, const void *buf, size_t bytes, void *stream,
+                      ktune_search **out) {
+  if (!s || !m || !buf || !out) FAIL(KTUNE_EINVAL, "null argument");
+  *out = nullptr;
+  CkptHeader hd;
+  if (bytes < sizeof(hd)) FAIL(KTUNE_EINVAL, "checkpoint truncated");
+  memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kCkptMagic || hd.version != kCkptVersion) FAIL(KTUNE_EINVAL, "not a search checkpoint");
+  if (hd.n_valid != s->n_valid || hd.n_raw != s->sa.n_raw || hd.n_params != s->sa.P ||
+      hd.space_hash != space_hash(s))
+    FAIL(KTUNE_EINVAL, "checkpoint belongs to another tuning space");
+  if (hd.K != m->K || hd.depth != m->D || hd.kind != m->kind)
+    FAIL(KTUNE_EMODEL, "checkpoint belongs to another model");
+  if (hd.n_last < 0 || hd.n_last > KTUNE_MAX_K || hd.n_evaluated < 1 || hd.n_evaluated > s->n_valid ||
+      hd.cprof_raw < 0 || hd.cprof_raw >= s->sa.n_raw)
+    FAIL(KTUNE_EINVAL, "checkpoint fields out of range");
+  ktune_search *h = nullptr;
+  const size_t need = sizeof(hd) + (size_t)hd.n_last * 16 + (size_t)((s->n_valid + 31) / 32) * 4;
+  if (bytes < need) FAIL(KTUNE_EINVAL, "checkpoint truncated");
+  TRY(ktune_search_create(s, m, &hd.opts, stream, &h));
+  const uint8_t *p = static_cast<const uint8_t *>(buf) + sizeof(hd);
+  h->last_raw.assign(reinterpret_cast<const int64_t *>(p), reinterpret_cast<const int64_t *>(p) + hd.n_last);
+  h->last_packed.assign(reinterpret_cast<const uint64_t *>(p + (size_t)hd.n_last * 8),
+                        reinterpret_cast<const uint64_t *>(p + (size_t)hd.n_last * 8) + hd.n_last);
+  p += (size_t)hd.n_last * 16;
+  const size_t words = (size_t)((s->n_valid + 31) / 32);
+  if (cudaMemcpyAsync(h->d_eval, p, words * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    ktune_search_destroy(h);
+    FAIL(KTUNE_ECUDA, "checkpoint upload failed");
+  }
+  h->cprof_raw = hd.cprof_raw;
+  h->cprof_packed = host_pack(s, hd.cprof_raw);
+  h->n_evaluated = hd.n_evaluated;
+  h->step_no = hd.step_no;
+  *out = h;
+  return KTUNE_OK;
+}
+
 int ktune_search_set_timing(ktune_search *h, int enable) {
   if (!h) FAIL(KTUNE_EINVAL, "null search");
   if (enable && !h->ev[0])
@@ -1142,14 +1262,19 @@ constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants
 int batch_items(ktune_batch *b) {
   std::vector<ItemDev> items;
   int64_t total = 0;
-  for (ktune_search *h : b->s) total += b->mode == 2 ? h->space->n_tiles : h->space->n_valid;
+  for (ktune_search *h : b->s)
+    if (h->model->kind != 2) total += b->mode == 2 ? h->space->n_tiles : h->space->n_valid;
   const int64_t target =
       std::max<int64_t>(b->mode == 2 ? 1 : 1024, total / ((int64_t)b->num_sms * b->items_per_cta));
   for (size_t i = 0; i < b->s.size(); ++i) {
     ktune_search *h = b->s[i];
+    b->sdh[i].item_begin = (int64_t)items.size();
+    if (h->model->kind == 2) {   // scored by the MLP kernels, no tree-walk items
+      b->sdh[i].item_end = (int64_t)items.size();
+      continue;
+    }
     const int64_t units = b->mode == 2 ? h->space->n_tiles : h->space->n_valid;
     const int64_t pieces = std::max<int64_t>(1, (units + target - 1) / target);
-    b->sdh[i].item_begin = (int64_t)items.size();
     for (int64_t q = 0; q < pieces; ++q) {
       ItemDev it{};
       it.search = (int)i;
@@ -1168,9 +1293,9 @@ int batch_items(ktune_batch *b) {
   b->d_cand_key = nullptr;
   b->d_cand_raw = nullptr;
   int rc;
-  if ((rc = dalloc(&b->d_items, items.size())) ||
-      (rc = dalloc(&b->d_cand_key, items.size() * KTUNE_MAX_K)) ||
-      (rc = dalloc(&b->d_cand_raw, items.size() * KTUNE_MAX_K)))
+  const size_t n_alloc = std::max<size_t>(1, items.size());
+  if ((rc = dalloc(&b->d_items, n_alloc)) || (rc = dalloc(&b->d_cand_key, n_alloc * KTUNE_MAX_K)) ||
+      (rc = dalloc(&b->d_cand_raw, n_alloc * KTUNE_MAX_K)))
     return rc;
   for (size_t i = 0; i < b->s.size(); ++i) {
     // candidates of search i live after those of the searches before it; the
@@ -1178,8 +1303,9 @@ int batch_items(ktune_batch *b) {
     b->sdh[i].cand_key = b->d_cand_key + b->sdh[i].item_begin * KTUNE_MAX_K;
     b->sdh[i].cand_raw = b->d_cand_raw + b->sdh[i].item_begin * KTUNE_MAX_K;
   }
-  CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(ItemDev),
-                     cudaMemcpyHostToDevice, b->stream));
+  if (!items.empty())
+    CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(ItemDev),
+                       cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->d_srch, b->sdh.data(), b->sdh.size() * sizeof(SearchDev),
                      cudaMemcpyHostToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
@@ -1218,9 +1344,22 @@ int batch_fill_steps(ktune_batch *b, const float *const *counters, int k, StepBa
 void batch_launch(ktune_batch *b, const StepBatch<kMaxBatch> &sb, cudaStream_t st, bool score_only) {
   const int S = (int)b->s.size();
   launch_bprep<kMaxBatch>(b->d_srch, b->d_steps, sb, S, b->K_max, b->D_max, st);
-  launch_bscore(b->d_srch, b->d_steps, b->d_items, b->n_items, b->mode, b->topk, b->grid, st,
-                b->variant);
+  if (b->n_items > 0)
+    launch_bscore(b->d_srch, b->d_steps, b->d_items, b->n_items, b->mode, b->topk, b->grid, st,
+                  b->variant);
   if (score_only) return;
+  // searches scored by the MLP: prediction of c_profile, then the fused
+  // tensor-core forward + Eq. score over all of TS (the same kernels as a
+  // single MLP step)
+  for (int i = 0; i < S; ++i) {
+    ktune_search *h = b->s[i];
+    if (h->model->kind != 2) continue;
+    const MlpDev md = h->model->mlp->dev();
+    launch_mlp_fwd(0, md, &b->d_steps[i].cprof_packed, 1, h->d_pcprof, nullptr, nullptr, nullptr,
+                   nullptr, h->model->mlp->d_status, 1, st);
+    launch_mlp_fwd(1, md, h->space->d_packed, h->space->n_valid, h->d_s, h->d_pcprof, h->d_delta,
+                   h->d_eval, h->d_mm, h->model->mlp->d_status, b->num_sms, st);
+  }
   if (!b->topk) launch_bweights(b->d_srch, b->d_sub_search, b->n_sub, st);
   launch_bselect(b->d_srch, b->d_steps, S, st);
 }
@@ -1242,12 +1381,19 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
   if (!searches || !out || n < 1) FAIL(KTUNE_EINVAL, "null argument or empty batch");
   if (n > kMaxBatch) FAIL(KTUNE_EINVAL, "more than 64 searches in a batch");
   *out = nullptr;
+  int tree0 = -1;   // first search scored by trees (its space mode is the batch's)
   for (int i = 0; i < n; ++i) {
     if (!searches[i]) FAIL(KTUNE_EINVAL, "null search");
-    if (searches[i]->model->kind != 1) FAIL(KTUNE_ESTATE, "batches take tree models only");
-    if (searches[i]->mode != searches[0]->mode || searches[i]->opts.select != searches[0]->opts.select)
-      FAIL(KTUNE_EINVAL, "searches of a batch must share the space mode and the select mode");
+    if (searches[i]->opts.select != searches[0]->opts.select)
+      FAIL(KTUNE_EINVAL, "searches of a batch must share the select mode");
+    if (searches[i]->model->kind == 1 && tree0 < 0) tree0 = i;
   }
+  for (int i = 0; i < n; ++i)
+    if (searches[i]->model->kind == 1 && searches[i]->mode != searches[tree0]->mode)
+      FAIL(KTUNE_EINVAL, "tree-scored searches of a batch must share the space mode");
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      if (searches[i] == searches[j]) FAIL(KTUNE_EINVAL, "a search appears twice in the batch");
   ktune_batch *b = new (std::nothrow) ktune_batch();
   if (!b) FAIL(KTUNE_ENOMEM, "host allocation");
   auto fail = [&](int rc) {
@@ -1255,7 +1401,7 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
     return rc;
   };
   b->s.assign(searches, searches + n);
-  b->mode = searches[0]->mode;
+  b->mode = tree0 >= 0 ? searches[tree0]->mode : 0;
   b->topk = searches[0]->opts.select == KTUNE_SELECT_TOPK;
   b->stream = (cudaStream_t)stream;
   int dev = 0;
@@ -1265,7 +1411,7 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
   for (int i = 0; i < n; ++i) {
     ktune_search *h = searches[i];
     b->K_max = std::max(b->K_max, h->model->K);
-    b->D_max = std::max(b->D_max, h->model->D);
+    if (h->model->kind == 1) b->D_max = std::max(b->D_max, h->model->D);
     SearchDev sd = h->sdh;
     sd.sub_begin = (int64_t)sub_search.size();
     for (int64_t g = 0; g < h->n_sub; ++g) sub_search.push_back(i);
@@ -1358,6 +1504,15 @@ int ktune_batch_step(ktune_batch *b, const float *const *counters, int k, int64_
   CK(cudaMemcpyAsync(b->h_out_packed, b->d_out_packed, (size_t)S * KTUNE_MAX_K * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(b->h_nout, b->d_nout, (size_t)S * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  for (ktune_search *h : b->s)
+    if (h->model->kind == 2) {
+      int status = 0;
+      CK(cudaMemcpy(&status, h->model->mlp->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+      if (status) {
+        cudaMemset(h->model->mlp->d_status, 0, sizeof(int));
+        FAIL(KTUNE_ETIMEOUT, "a tensor-core wait of the MLP timed out");
+      }
+    }
   bool exhausted = false;
   for (int i = 0; i < S; ++i) {
     ktune_search *h = b->s[i];

@@ -101,6 +101,7 @@ struct SearchDev {
   uint8_t inc128[KTUNE_MAX_PARAMS];
   const uint8_t *nodes;
   const float *leaves;
+  int kind;                   // model kind: 1 trees, 2 MLP (scored by its own kernels)
   int K, D;
   uint8_t roles[KTUNE_MAX_COUNTERS];
   double inst_reaction, cores;

@@ -71,6 +71,25 @@ __global__ void __launch_bounds__(256) k_bprep(const SearchDev *__restrict__ src
   const SearchDev &sd = srch[blockIdx.z];
   const StepDev &st = sb.st[blockIdx.z];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) steps_dev[blockIdx.z] = st;
+  if (sd.kind == 2) {
+    // a search scored by the MLP: only the step's set-up here (one CTA); its
+    // prediction and scoring kernels follow in the same launch sequence
+    if (blockIdx.x != 0 || blockIdx.y != 0) return;
+    if (threadIdx.x == 0) {
+      sd.mm[0] = INT_MAX;
+      sd.mm[1] = INT_MIN;
+      if (st.n_out) *st.n_out = 0;
+      int na = 0;
+      for (int c = 0; c < sd.K; ++c) na += st.delta[c] != 0.0f;
+      *sd.n_active = na;
+    }
+    for (int c = threadIdx.x; c < sd.K; c += blockDim.x) sd.delta[c] = st.delta[c];
+    if (sd.select == KTUNE_SELECT_SAMPLE) {
+      const int64_t n_super = ((sd.N + kSubTile - 1) / kSubTile + kSuper - 1) / kSuper;
+      for (int64_t i = threadIdx.x; i < n_super; i += blockDim.x) sd.super_sum[i] = 0;
+    }
+    return;
+  }
   const int K = sd.K, D = sd.D, L = 1 << D;
   const int p = blockIdx.x;
   if (p >= K || (int)blockIdx.y * kPrepLeavesB >= L) return;

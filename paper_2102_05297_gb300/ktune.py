@@ -70,6 +70,8 @@ _SIGS = {
     "ktune_search_evaluated": ([_vp, _i64p], C.c_int),
     "ktune_search_stats": ([_vp, C.POINTER(ktune_step_stats)], C.c_int),
     "ktune_search_set_timing": ([_vp, C.c_int], C.c_int),
+    "ktune_search_save": ([_vp, _vp, C.POINTER(C.c_size_t)], C.c_int),
+    "ktune_search_load": ([_vp, _vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)], C.c_int),
     "ktune_batch_create": ([C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)], C.c_int),
     "ktune_batch_destroy": ([_vp], C.c_int),
     "ktune_batch_step": ([_vp, C.POINTER(_f32p), C.c_int, _i64p, _f32p, _i32p], C.c_int),
@@ -294,6 +296,31 @@ class Search:
 
     def set_timing(self, enable: bool = True):
         check(lib.ktune_search_set_timing(self.h, int(enable)), "ktune_search_set_timing")
+
+    def save(self) -> bytes:
+        """The search's checkpoint (ktune_search_save)."""
+        n = C.c_size_t(0)
+        check(lib.ktune_search_save(self.h, None, C.byref(n)), "ktune_search_save")
+        buf = C.create_string_buffer(n.value)
+        check(lib.ktune_search_save(self.h, buf, C.byref(n)), "ktune_search_save")
+        return buf.raw[:n.value]
+
+    @classmethod
+    def load(cls, space: Space, model: Model, blob: bytes, stream=None) -> "Search":
+        """A search restored from a checkpoint (ktune_search_load)."""
+        self = cls.__new__(cls)
+        h = C.c_void_p()
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib.ktune_search_load(space.h, model.h, buf, len(blob), _stream_ptr(stream),
+                                    C.byref(h)), "ktune_search_load")
+        self.h = h
+        hdr_k = int.from_bytes(blob[40:44], "little")   # opts.k
+        self.k = hdr_k
+        self.K = model.K
+        self.space, self.model = space, model
+        self._raw = np.empty(64, np.int64)
+        self._score = np.empty(64, np.float32)
+        return self
 
     def close(self):
         if getattr(self, "h", None):

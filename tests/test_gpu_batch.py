@@ -97,3 +97,39 @@ def test_batch_rejects_mixed_modes(kt):
     e2 = make(kt, kt.KTUNE_SELECT_TOPK, 0, per_space=1, names=SPACES[:1])
     with pytest.raises(kt.KtuneError):
         kt.Batch([e1[0][4], e2[0][4]])
+
+
+def make_mixed(kt, stream=None):
+    """Searches over three spaces, each space searched by a tree-scored and
+    an MLP-scored search (untrained seeded network), in one list."""
+    from paper_2102_05297_gb300 import fit
+    out, keep = [], []
+    for si, name in enumerate(["batch_2", "batch_3", "batch_6"]):
+        d = W.load_space(name)
+        K = [16, 32, 40][si]
+        roles = W.layout(K)
+        gpu = SyntheticGPU(d, roles, seed=si)
+        sp = kt.Space.from_desc(d)
+        tm = kt.Model(sp, random_model(d.radices, roles, depth=10, seed=200 + si))
+        mlp = kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=64)
+        p = fit.init_mlp(mlp.F, K, seed=si)
+        p["b4"] = np.full(K, 0.5, np.float32)        # predictions mostly positive
+        mlp.set_params(p)
+        mm = kt.Model.from_mlp(mlp)
+        keep += [sp, tm, mlp, mm]
+        for r, model in enumerate((tm, mm)):
+            s = kt.Search(sp, model, k=5, seed=30 + 10 * si + r, search_id=r, stream=stream)
+            out.append((d, gpu, sp, model, s))
+    return out, keep
+
+
+def test_mixed_tree_and_mlp_batch_matches_single_searches(kt):
+    """Tree-scored and MLP-scored searches in one batch (one CUDA graph per
+    step) reproduce the same searches stepped one at a time."""
+    import torch
+    stream = torch.cuda.Stream()
+    a, keep_a = make_mixed(kt, stream=stream)
+    b, keep_b = make_mixed(kt)
+    got = run_batch(kt, a, 4, 5, stream=stream)
+    ref = run_single(b, 4, 5)
+    assert got == ref

@@ -296,4 +296,4 @@ def test_mlp_model_rules(kt):
         kt.Search(otf, kt.Model.from_mlp(m2), k=5)
     s = kt.Search(sp, model, k=5)
     with pytest.raises(kt.KtuneError):
-        kt.Batch([s])
+        kt.Batch([s, s])                      # the same search twice
