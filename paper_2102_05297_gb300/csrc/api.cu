@@ -1351,14 +1351,21 @@ void batch_launch(ktune_batch *b, const StepBatch<kMaxBatch> &sb, cudaStream_t s
   // searches scored by the MLP: prediction of c_profile, then the fused
   // tensor-core forward + Eq. score over all of TS (the same kernels as a
   // single MLP step)
-  for (int i = 0; i < S; ++i) {
-    ktune_search *h = b->s[i];
-    if (h->model->kind != 2) continue;
+  for (const auto &g : b->mlp_groups) {
+    const ktune_search *h = g.first;
     const MlpDev md = h->model->mlp->dev();
-    launch_mlp_fwd(0, md, &b->d_steps[i].cprof_packed, 1, h->d_pcprof, nullptr, nullptr, nullptr,
-                   nullptr, h->model->mlp->d_status, 1, st);
-    launch_mlp_fwd(1, md, h->space->d_packed, h->space->n_valid, h->d_s, h->d_pcprof, h->d_delta,
-                   h->d_eval, h->d_mm, h->model->mlp->d_status, b->num_sms, st);
+    const int S = (int)g.members.size();
+    launch_mlp_fwd(0, md, g.d_cprof, S, g.d_pcprof, nullptr, nullptr, nullptr, nullptr,
+                   h->model->mlp->d_status, 1, st);
+    if (mlp_pipe_supported(md.F) && md.wc)
+      launch_mlp_score_shared(md, h->space->d_packed, h->space->n_valid, g.tg,
+                              h->model->mlp->d_status, b->num_sms, st);
+    else
+      for (int q = 0; q < S; ++q) {
+        ktune_search *m = b->s[g.members[q]];
+        launch_mlp_fwd(1, md, h->space->d_packed, h->space->n_valid, m->d_s, g.tg.pcprof[q],
+                       m->d_delta, m->d_eval, m->d_mm, h->model->mlp->d_status, b->num_sms, st);
+      }
   }
   if (!b->topk) launch_bweights(b->d_srch, b->d_sub_search, b->n_sub, st);
   launch_bselect(b->d_srch, b->d_steps, S, st);
@@ -1419,6 +1426,35 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
   }
   b->n_sub = (int64_t)sub_search.size();
   int rc;
+  for (int i = 0; i < n; ++i) {
+    ktune_search *h = searches[i];
+    if (h->model->kind != 2) continue;
+    ktune_batch::MlpGroup *g = nullptr;
+    for (auto &e : b->mlp_groups)
+      if (e.first->model->mlp == h->model->mlp && e.first->space == h->space &&
+          (int)e.members.size() < kMlpMaxShare)
+        g = &e;
+    if (!g) {
+      b->mlp_groups.emplace_back();
+      g = &b->mlp_groups.back();
+      g->first = h;
+    }
+    g->members.push_back(i);
+  }
+  for (auto &g : b->mlp_groups) {
+    const int S = (int)g.members.size(), K = g.first->model->K;
+    if ((rc = dalloc(&g.d_cprof, S)) || (rc = dalloc(&g.d_pcprof, (size_t)S * K))) return fail(rc);
+    g.tg.S = S;
+    for (int q = 0; q < S; ++q) {
+      ktune_search *m = searches[g.members[q]];
+      b->sdh[g.members[q]].cprof_slot = g.d_cprof + q;
+      g.tg.pcprof[q] = g.d_pcprof + (size_t)q * K;
+      g.tg.delta[q] = m->d_delta;
+      g.tg.s[q] = m->d_s;
+      g.tg.eval[q] = m->d_eval;
+      g.tg.mm[q] = m->d_mm;
+    }
+  }
   if ((rc = dalloc(&b->d_srch, n)) || (rc = dalloc(&b->d_steps, n)) ||
       (rc = dalloc(&b->d_sub_search, sub_search.size())) ||
       (rc = dalloc(&b->d_out_raw, (size_t)n * KTUNE_MAX_K)) ||
@@ -1449,6 +1485,10 @@ int ktune_batch_destroy(ktune_batch *b) {
   for (void *p : dev) cudaFree(p);
   void *pin[] = {b->h_out_raw, b->h_out_score, b->h_out_packed, b->h_nout};
   for (void *p : pin) cudaFreeHost(p);
+  for (auto &g : b->mlp_groups) {
+    cudaFree(g.d_cprof);
+    cudaFree(g.d_pcprof);
+  }
   batch_drop_graph(b);
   delete b;
   return KTUNE_OK;

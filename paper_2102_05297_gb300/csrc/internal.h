@@ -102,6 +102,7 @@ struct SearchDev {
   const uint8_t *nodes;
   const float *leaves;
   int kind;                   // model kind: 1 trees, 2 MLP (scored by its own kernels)
+  uint64_t *cprof_slot;       // batched MLP search: where the prepare kernel puts c_profile
   int K, D;
   uint8_t roles[KTUNE_MAX_COUNTERS];
   double inst_reaction, cores;
@@ -226,6 +227,21 @@ struct EpiArgs {
   int ldat = 0;
 };
 
+// The searches one scoring launch of the MLP serves (they share the network
+// and the space): per search its predicted c_profile counters, its Delta, its
+// score array, evaluated bits and ordered-int min / max.
+constexpr int kMlpMaxShare = 8;
+struct MlpTargets {
+  int S;
+  const float *pcprof[kMlpMaxShare];
+  const float *delta[kMlpMaxShare];
+  float *s[kMlpMaxShare];
+  const uint32_t *eval[kMlpMaxShare];
+  int *mm[kMlpMaxShare];
+};
+void launch_mlp_score_shared(const MlpDev &md, const uint64_t *packed, int64_t n,
+                             const MlpTargets &tg, int *status, int max_ctas, cudaStream_t st);
+
 int mlp_fwd_smem(int F);
 bool mlp_pipe_supported(int F);
 void mlp_pipe_set_attrs();
@@ -344,6 +360,16 @@ struct ktune_batch {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphNode_t prep_node = nullptr;
   cudaStream_t graph_stream = nullptr;
+  // MLP-scored searches sharing (network, space), at most kMlpMaxShare per
+  // group: one c_profile prediction and one scoring pass serve the group
+  struct MlpGroup {
+    ktune_search *first = nullptr;
+    std::vector<int> members;
+    uint64_t *d_cprof = nullptr;   // [S] c_profiles, written by the prepare kernel
+    float *d_pcprof = nullptr;     // [S][K] their predicted counters
+    ktune::MlpTargets tg{};
+  };
+  std::vector<MlpGroup> mlp_groups;
 };
 
 struct ktune_search {

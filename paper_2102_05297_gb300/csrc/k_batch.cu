@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) k_bprep(const SearchDev *__restrict__ src
     // prediction and scoring kernels follow in the same launch sequence
     if (blockIdx.x != 0 || blockIdx.y != 0) return;
     if (threadIdx.x == 0) {
+      if (sd.cprof_slot) *sd.cprof_slot = st.cprof_packed;
       sd.mm[0] = INT_MAX;
       sd.mm[1] = INT_MIN;
       if (st.n_out) *st.n_out = 0;

@@ -125,15 +125,14 @@ __device__ __forceinline__ int layer_n(const MlpDev &md, int l) { return l == 3 
 template <int MODE>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     k_mlp_pipe(const MlpDev md, const uint64_t *__restrict__ packed, int64_t n,
-               float *__restrict__ out, const float *__restrict__ pcprof,
-               const float *__restrict__ delta, const uint32_t *__restrict__ evaluated,
-               int *__restrict__ minmax, int *status) {
+               float *__restrict__ out, const __grid_constant__ MlpTargets tg, int *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t *ring = sm + 2 * kActBytes;
   __shared__ uint64_t full[kMlpStages], empty[kMlpStages], acc_full[2], act_ready[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ __align__(16) float sh_b[3 * kMlpHidden + 64];
-  __shared__ float sh_rng[KTUNE_MAX_COUNTERS], sh_pc[KTUNE_MAX_COUNTERS], sh_dl[KTUNE_MAX_COUNTERS];
+  __shared__ float sh_rng[KTUNE_MAX_COUNTERS];
+  __shared__ float sh_pc[kMlpMaxShare][KTUNE_MAX_COUNTERS], sh_dl[kMlpMaxShare][KTUNE_MAX_COUNTERS];
   __shared__ int sh_off[KTUNE_MAX_PARAMS + 1];
   __shared__ uint16_t sh_utab[KTUNE_MAX_PARAMS * 16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -157,11 +156,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
   for (int i = threadIdx.x; i < 3 * kMlpHidden; i += blockDim.x) sh_b[i] = md.b[i >> 8][i & 255];
   for (int i = threadIdx.x; i < md.Kp; i += blockDim.x) sh_b[3 * kMlpHidden + i] = md.b[3][i];
-  for (int i = threadIdx.x; i < md.K; i += blockDim.x) {
-    sh_rng[i] = md.range[i];
-    sh_pc[i] = MODE == 1 ? pcprof[i] : 0.0f;
-    sh_dl[i] = MODE == 1 ? delta[i] : 0.0f;
-  }
+  for (int i = threadIdx.x; i < md.K; i += blockDim.x) sh_rng[i] = md.range[i];
+  if (MODE == 1)
+    for (int i = threadIdx.x; i < tg.S * md.K; i += blockDim.x) {
+      const int q = i / md.K, c = i - q * md.K;
+      sh_pc[q][c] = tg.pcprof[q][c];
+      sh_dl[q][c] = tg.delta[q][c];
+    }
   for (int i = threadIdx.x; i <= md.P; i += blockDim.x) sh_off[i] = md.off[i];
   for (int i = threadIdx.x; i < md.P * 16; i += blockDim.x) sh_utab[i] = md.utab[i];
   tc::fence_before();
@@ -254,7 +255,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     const int F = md.F;
     bool ok = true;
     uint32_t aph = 0u;
-    float s_mn = INFINITY, s_mx = -INFINITY;
+    // running min / max of the scores of the searches this warp scores (q = cg, cg + 2, ...)
+    float s_mn[kMlpMaxShare / 2], s_mx[kMlpMaxShare / 2];
+#pragma unroll
+    for (int u = 0; u < kMlpMaxShare / 2; ++u) {
+      s_mn[u] = INFINITY;
+      s_mx[u] = -INFINITY;
+    }
     auto tile_of = [&](int64_t p) -> int64_t {
       const int64_t j = 2 * p + x;
       return j < my_tiles ? (int64_t)blockIdx.x + j * (int64_t)gridDim.x : -1;
@@ -317,11 +324,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         } else {
           const bool more = p + 1 < n_pairs;
           const uint64_t pk_next = more ? fetch(tile_of(p + 1)) : 0ull;   // in flight meanwhile
-          if (cg == 0) {
+          // output layer: warps of column group cg score the searches q = cg, cg + 2, ...
+          // (all searches are scored from the same predicted counters)
+          if (MODE == 0 ? cg == 0 : cg < tg.S) {
             const int64_t i = tile >= 0 ? tile * 128 + row : -1;
             const bool valid = i >= 0 && i < n;
             const float *b4 = sh_b + 3 * kMlpHidden;
-            float s = 0.0f;
+            float sq[kMlpMaxShare / 2];
+#pragma unroll
+            for (int u = 0; u < kMlpMaxShare / 2; ++u) sq[u] = 0.0f;
             for (int c0 = 0; c0 < md.Kp; c0 += 16) {
               float v[16];
               tc::tmem_ld16(tacc + c0, v);
@@ -333,20 +344,30 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                 if (MODE == 0) {
                   if (valid) out[(size_t)i * md.K + c] = a;
                 } else {
-                  const float A = sh_pc[c], dl = sh_dl[c];
-                  const float den = __fadd_rn(a, A);
-                  float t = 0.0f;
-                  if (dl != 0.0f && A != 0.0f && a != 0.0f && den != 0.0f)
-                    t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(a, A), den));
-                  s = __fadd_rn(s, t);
+#pragma unroll
+                  for (int u = 0; u < kMlpMaxShare / 2; ++u) {
+                    const int q = cg + 2 * u;
+                    if (q >= tg.S) break;
+                    const float A = sh_pc[q][c], dl = sh_dl[q][c];
+                    const float den = __fadd_rn(a, A);
+                    float t = 0.0f;
+                    if (dl != 0.0f && A != 0.0f && a != 0.0f && den != 0.0f)
+                      t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(a, A), den));
+                    sq[u] = __fadd_rn(sq[u], t);
+                  }
                 }
               }
             }
             if (MODE == 1 && valid) {
-              out[i] = s;
-              if (!((evaluated[i >> 5] >> (i & 31)) & 1u)) {
-                s_mn = fminf(s_mn, s);
-                s_mx = fmaxf(s_mx, s);
+#pragma unroll
+              for (int u = 0; u < kMlpMaxShare / 2; ++u) {
+                const int q = cg + 2 * u;
+                if (q >= tg.S) break;
+                tg.s[q][i] = sq[u];
+                if (!((tg.eval[q][i >> 5] >> (i & 31)) & 1u)) {
+                  s_mn[u] = fminf(s_mn[u], sq[u]);
+                  s_mx[u] = fmaxf(s_mx[u], sq[u]);
+                }
               }
             }
           }
@@ -357,13 +378,19 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     if (!ok) {
       if (lane == 0) atomicExch(status, KTUNE_ETIMEOUT);
     } else if (MODE == 1) {
-      for (int o = 16; o; o >>= 1) {
-        s_mn = fminf(s_mn, __shfl_xor_sync(FULL, s_mn, o));
-        s_mx = fmaxf(s_mx, __shfl_xor_sync(FULL, s_mx, o));
-      }
-      if (lane == 0 && s_mn <= s_mx) {
-        atomicMin(minmax, okey_p(s_mn));
-        atomicMax(minmax + 1, okey_p(s_mx));
+#pragma unroll
+      for (int u = 0; u < kMlpMaxShare / 2; ++u) {
+        const int q = cg + 2 * u;
+        if (q >= tg.S) break;
+        float mn = s_mn[u], mx = s_mx[u];
+        for (int o = 16; o; o >>= 1) {
+          mn = fminf(mn, __shfl_xor_sync(FULL, mn, o));
+          mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+        }
+        if (lane == 0 && mn <= mx) {
+          atomicMin(tg.mm[q], okey_p(mn));
+          atomicMax(tg.mm[q] + 1, okey_p(mx));
+        }
       }
     }
   }
@@ -406,13 +433,28 @@ void launch_mlp_pipe(int mode, const MlpDev &md, const uint64_t *packed, int64_t
   const int64_t tiles = (n + 127) / 128;
   if (tiles == 0) return;
   const int64_t pairs = (tiles + 1) / 2;
-  int grid = (int)std::min<int64_t>(pairs, max_ctas > 0 ? max_ctas : pairs);
-  if (mode == 0)
-    k_mlp_pipe<0><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, out, pcprof, delta,
-                                                          evaluated, minmax, status);
-  else
-    k_mlp_pipe<1><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, out, pcprof, delta,
-                                                          evaluated, minmax, status);
+  const int grid = (int)std::min<int64_t>(pairs, max_ctas > 0 ? max_ctas : pairs);
+  MlpTargets tg{};
+  if (mode == 0) {
+    k_mlp_pipe<0><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, out, tg, status);
+  } else {
+    tg.S = 1;
+    tg.pcprof[0] = pcprof;
+    tg.delta[0] = delta;
+    tg.s[0] = out;
+    tg.eval[0] = evaluated;
+    tg.mm[0] = minmax;
+    k_mlp_pipe<1><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, out, tg, status);
+  }
+}
+
+void launch_mlp_score_shared(const MlpDev &md, const uint64_t *packed, int64_t n,
+                             const MlpTargets &tg, int *status, int max_ctas, cudaStream_t st) {
+  const int64_t tiles = (n + 127) / 128;
+  if (tiles == 0 || tg.S < 1) return;
+  const int64_t pairs = (tiles + 1) / 2;
+  const int grid = (int)std::min<int64_t>(pairs, max_ctas > 0 ? max_ctas : pairs);
+  k_mlp_pipe<1><<<grid, kPipeThreads, kPipeSmem, st>>>(md, packed, n, nullptr, tg, status);
 }
 
 }  // namespace ktune

@@ -100,8 +100,9 @@ def test_batch_rejects_mixed_modes(kt):
 
 
 def make_mixed(kt, stream=None):
-    """Searches over three spaces, each space searched by a tree-scored and
-    an MLP-scored search (untrained seeded network), in one list."""
+    """Searches over three spaces, each space searched by two tree-scored and
+    three MLP-scored searches (one untrained seeded network per space, whose
+    scoring pass the three share in a batch), in one list."""
     from paper_2102_05297_gb300 import fit
     out, keep = [], []
     for si, name in enumerate(["batch_2", "batch_3", "batch_6"]):
@@ -117,7 +118,7 @@ def make_mixed(kt, stream=None):
         mlp.set_params(p)
         mm = kt.Model.from_mlp(mlp)
         keep += [sp, tm, mlp, mm]
-        for r, model in enumerate((tm, mm)):
+        for r, model in enumerate((tm, mm, mm, tm, mm)):   # three MLP searches share one pass
             s = kt.Search(sp, model, k=5, seed=30 + 10 * si + r, search_id=r, stream=stream)
             out.append((d, gpu, sp, model, s))
     return out, keep
