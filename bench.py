@@ -145,6 +145,20 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+def combine_ranks(dist, t_total, t_e2e, scored, device):
+    """Whole-job figures of independent replicas (one search per rank, seed =
+    rank, no data exchanged): the slowest rank's device and end-to-end times,
+    and the configurations scored by all ranks."""
+    if dist is None:
+        return t_total, t_e2e, float(scored)
+    import torch
+    tt = torch.tensor([t_total, t_e2e], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cnt = torch.tensor([float(scored)], dtype=torch.float64, device=device)
+    dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(tt[1]), float(cnt[0])
+
+
 def setup(kt, name, seed):
     wl = WORKLOADS[name]
     desc = load_desc(wl)
@@ -269,14 +283,7 @@ def run_ours(args):
             e2e_ms.append((t1 - t0) * 1e3)
     s2.close()
 
-    if dist:
-        tt = torch.tensor([t_total, sum(e2e_ms) / 1e3], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        cnt = torch.tensor([scored], dtype=torch.float64, device="cuda")
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-        t_total, t_e2e, scored_all = float(tt[0]), float(tt[1]), float(cnt[0])
-    else:
-        t_e2e, scored_all = sum(e2e_ms) / 1e3, float(scored)
+    t_total, t_e2e, scored_all = combine_ranks(dist, t_total, sum(e2e_ms) / 1e3, scored, "cuda")
 
     pk, src = peaks()
     props = torch.cuda.get_device_properties(local)
