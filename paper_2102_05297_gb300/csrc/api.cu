@@ -172,6 +172,38 @@ int build_groups(ktune_space *s, const int32_t *code, int n) {
   return KTUNE_OK;
 }
 
+// Constrained-index table (see kCiMaxBits): built when the constrained
+// parameters' value combinations number at most kCiMaxBits and there is at
+// least one constraint; every combination is checked against every group's
+// table.
+void build_ci(ktune_space *s) {
+  if (s->groups.empty()) return;
+  uint32_t used = 0;
+  for (const GroupDev &g : s->groups)
+    for (int i = 0; i < g.n; ++i) used |= 1u << g.param[i];
+  int64_t prod = 1;
+  for (int j = s->sa.P - 1; j >= 0; --j)
+    if ((used >> j) & 1u) {
+      s->ci_stride[j] = (uint32_t)prod;
+      prod *= s->sa.radix[j];
+      if (prod > kCiMaxBits) {
+        for (int q = 0; q < KTUNE_MAX_PARAMS; ++q) s->ci_stride[q] = 0;
+        return;
+      }
+    }
+  s->ci_table.assign((size_t)((prod + 31) / 32), 0u);
+  for (int64_t c = 0; c < prod; ++c) {
+    uint64_t p = 0;   // packed digits of a configuration with this constrained combination
+    int64_t rem = c;
+    for (int j = s->sa.P - 1; j >= 0; --j)
+      if ((used >> j) & 1u) {
+        p |= (uint64_t)(rem % s->sa.radix[j]) << (4 * j);
+        rem /= s->sa.radix[j];
+      }
+    if (ktune::host_valid(s, p)) s->ci_table[(size_t)(c >> 5)] |= 1u << (c & 31);
+  }
+}
+
 // Window tables of the one-word layout (see WinDev): groups in program order
 // join the current window while the union of their parameters' digit widths
 // stays within kWinBits; each window's table holds, for every value of its
@@ -444,12 +476,23 @@ int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune
     }
     s->narrow = bits <= 32;
   }
-  if (s->narrow) build_windows(s);
+  if (s->narrow) {
+    build_windows(s);
+    build_ci(s);
+  }
 
   cudaStream_t cs = (cudaStream_t)stream;
   if ((rc = dalloc(&s->d_groups, s->groups.size()))) return cleanup(rc);
   if ((rc = dalloc(&s->d_table, s->table.size()))) return cleanup(rc);
   if ((rc = dalloc(&s->d_win_table, std::max<size_t>(1, s->win_table.size())))) return cleanup(rc);
+  if (!s->ci_table.empty()) {
+    if ((rc = dalloc(&s->d_ci_table, s->ci_table.size()))) return cleanup(rc);
+    if (cudaMemcpyAsync(s->d_ci_table, s->ci_table.data(), s->ci_table.size() * 4,
+                        cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess) {
+      set_error("descriptor upload failed");
+      return cleanup(KTUNE_ECUDA);
+    }
+  }
   if (!s->win_table.empty() &&
       cudaMemcpyAsync(s->d_win_table, s->win_table.data(), s->win_table.size() * 4,
                       cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess) {
@@ -518,6 +561,7 @@ int ktune_space_destroy(ktune_space *s) {
   cudaFree(s->d_packed);
   cudaFree(s->d_narrow);
   cudaFree(s->d_win_table);
+  cudaFree(s->d_ci_table);
   cudaFree(s->d_tile_offset);
   delete s;
   return KTUNE_OK;
@@ -803,6 +847,9 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
     sd.pos[j] = s->pos[j];
     sd.width[j] = s->width[j];
   }
+  sd.ci_table = s->d_ci_table;
+  sd.ci_words = (int)s->ci_table.size();
+  for (int j = 0; j < KTUNE_MAX_PARAMS; ++j) sd.ci_stride[j] = s->ci_stride[j];
   sd.win_table = s->d_win_table;
   sd.n_win = (int)s->win.size();
   sd.win_words = (int)s->win_table.size();

@@ -74,6 +74,13 @@ constexpr int kOtfRun = 4;              // raw indices per thread per decode rou
 constexpr int kMaxWin = 16;             // window tables per space
 constexpr int kWinBits = 12;            // widest window index: 4096 bits
 constexpr int kWinWords = 2048;         // all window tables of a space, 32-bit words (8 KB)
+// Constrained-index table: when the parameters read by the constraints have
+// at most kCiMaxBits value combinations, one bit per combination (mixed radix
+// over those parameters, the last one fastest) says whether the constraints
+// hold; a configuration's bit is found from its "constrained index"
+// sum_j digit_j * ci_stride_j (ci_stride_j = 0 for unconstrained parameters),
+// which an odometer step changes by a per-parameter constant.
+constexpr int kCiMaxBits = 1 << 17;     // 16 KB table
 struct alignas(4) WinDev {
   uint8_t n, bits;                      // parameters, index bits
   uint16_t off;                         // first word of the table
@@ -99,6 +106,9 @@ struct SearchDev {
   WinDev win[kMaxWin];
   uint8_t generic[kMaxGroups];
   uint8_t inc128[KTUNE_MAX_PARAMS];
+  const uint32_t *ci_table;   // constrained-index table (null: use the windows)
+  int ci_words;
+  uint32_t ci_stride[KTUNE_MAX_PARAMS];
   const uint8_t *nodes;
   const float *leaves;
   int kind;                   // model kind: 1 trees, 2 MLP (scored by its own kernels)
@@ -318,6 +328,10 @@ struct ktune_space {
   std::vector<uint32_t> win_table;
   std::vector<uint8_t> generic;      // groups no window covers
   uint32_t *d_win_table = nullptr;
+  // constrained-index table (narrow spaces whose constrained combinations fit)
+  std::vector<uint32_t> ci_table;
+  uint32_t ci_stride[KTUNE_MAX_PARAMS] = {0};
+  uint32_t *d_ci_table = nullptr;
 };
 
 struct ktune_model {

@@ -286,10 +286,12 @@ __device__ __forceinline__ bool valid_word(const SearchDev &sd, uint32_t W) {
 struct OtfCtx {
   uint8_t pos[KTUNE_MAX_PARAMS], width[KTUNE_MAX_PARAMS], radix[KTUNE_MAX_PARAMS],
       inc[KTUNE_MAX_PARAMS];
+  uint32_t cis[KTUNE_MAX_PARAMS];   // constrained-index strides (ci_words > 0)
   WinDev win[kMaxWin];
-  int P, n_win, n_generic, inc_top;
+  int P, n_win, n_generic, inc_top, ci_words, pad_[3];
 };
-constexpr int kCtxMax = ((int)sizeof(OtfCtx) + kWinWords * 4 + 15) & ~15;
+constexpr int kCtxTable = kWinWords * 4 > kCiMaxBits / 8 ? kWinWords * 4 : kCiMaxBits / 8;
+constexpr int kCtxMax = ((int)sizeof(OtfCtx) + kCtxTable + 15) & ~15;
 static_assert(sizeof(OtfCtx) % 16 == 0, "window tables start 16-byte aligned");
 
 // Word of raw index `raw` (digits by division, last parameter fastest).
@@ -316,8 +318,9 @@ __device__ __forceinline__ uint32_t otf_next(const OtfCtx *c, uint32_t W) {
 }
 
 // Word of the raw index 128 further on: digit-wise addition of 128's digits
-// with carry, stopping once no digit or carry is left.
-__device__ __forceinline__ uint32_t otf_add128(const OtfCtx *c, uint32_t W) {
+// with carry, stopping once no digit or carry is left; x, the constrained
+// index, follows every digit that changes.
+__device__ __forceinline__ uint32_t otf_add128(const OtfCtx *c, uint32_t W, uint32_t &x) {
   uint32_t carry = 0;
   for (int j = c->P - 1; j >= 0; --j) {
     const uint32_t inc = c->inc[j] + carry;
@@ -326,10 +329,36 @@ __device__ __forceinline__ uint32_t otf_add128(const OtfCtx *c, uint32_t W) {
       continue;
     }
     const uint32_t sh = c->pos[j], m = (1u << c->width[j]) - 1u;
-    uint32_t d = ((W >> sh) & m) + inc;
+    const uint32_t d0 = (W >> sh) & m;
+    uint32_t d = d0 + inc;
     carry = d >= c->radix[j] ? 1u : 0u;
     if (carry) d -= c->radix[j];
+    x += (d - d0) * c->cis[j];   // modulo 2^32: exact for the true (non-negative) result
     W = (W & ~(m << sh)) | (d << sh);
+  }
+  return W;
+}
+
+// Constrained index of word W.
+__device__ __forceinline__ uint32_t otf_ci(const OtfCtx *c, uint32_t W) {
+  uint32_t x = 0;
+  for (int j = 0; j < c->P; ++j) x += ((W >> c->pos[j]) & ((1u << c->width[j]) - 1u)) * c->cis[j];
+  return x;
+}
+
+// Odometer step of W that also steps its constrained index x: the digit that
+// grows adds its stride, every digit that wraps from radix - 1 to 0 takes
+// (radix - 1) strides away.
+__device__ __forceinline__ uint32_t otf_next_ci(const OtfCtx *c, uint32_t W, uint32_t &x) {
+  for (int j = c->P - 1; j >= 0; --j) {
+    const uint32_t sh = c->pos[j], m = (1u << c->width[j]) - 1u;
+    const uint32_t d = ((W >> sh) & m) + 1u;
+    if (d < c->radix[j]) {
+      x += c->cis[j];
+      return W + (1u << sh);
+    }
+    x -= (d - 1u) * c->cis[j];
+    W &= ~(m << sh);
   }
   return W;
 }
@@ -457,6 +486,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         ctx->width[j] = sd.width[j];
         ctx->radix[j] = (uint8_t)sd.sa.radix[j];
         ctx->inc[j] = sd.inc128[j];
+        ctx->cis[j] = sd.ci_stride[j];
       }
       for (int i = threadIdx.x; i < (int)(sizeof(ctx->win) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t *>(ctx->win)[i] = reinterpret_cast<const uint32_t *>(sd.win)[i];
@@ -471,9 +501,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         ctx->n_win = sd.n_win;
         ctx->n_generic = sd.n_generic;
         ctx->inc_top = top;
+        ctx->ci_words = sd.ci_table ? sd.ci_words : 0;
       }
+      // the constrained-index table when the space has one, else the window tables
       uint32_t *tab = reinterpret_cast<uint32_t *>(ctx + 1);
-      for (int i = threadIdx.x; i < sd.win_words; i += blockDim.x) tab[i] = __ldg(sd.win_table + i);
+      if (sd.ci_table)
+        for (int i = threadIdx.x; i < sd.ci_words; i += blockDim.x) tab[i] = __ldg(sd.ci_table + i);
+      else
+        for (int i = threadIdx.x; i < sd.win_words; i += blockDim.x) tab[i] = __ldg(sd.win_table + i);
       __syncthreads();
     }
     if (topk) {
@@ -608,6 +643,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t *lr = ol_raw + warp * kWarpCap;
         int lcount = 0;
         const uint32_t n_raw = (uint32_t)sd.sa.n_raw;
+        const bool use_ci = ctx->ci_words > 0;
         const int64_t eval_words = (sd.N + 31) >> 5;
         auto walk_list = [&](int take) {
           uint32_t Wv[CPT];
@@ -640,16 +676,29 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
           int64_t ord_base = __ldg(sd.tile_offset + t);
           uint32_t W = otf_decode(ctx, tbase + 4u * (uint32_t)lane);
+          uint32_t xci = use_ci ? otf_ci(ctx, W) : 0u;
           for (int q = 0; q < kEnumTileRaw / 128; ++q) {
             const uint32_t rb = tbase + (uint32_t)q * 128u;
             if (rb >= n_raw) break;                       // warp-uniform
             const uint32_t r0 = rb + 4u * (uint32_t)lane;
             uint32_t Wq[4];
-            Wq[0] = W;
-#pragma unroll
-            for (int u = 1; u < 4; ++u) Wq[u] = otf_next(ctx, Wq[u - 1]);
             const int n_here = r0 >= n_raw ? 0 : (int)min(4u, n_raw - r0);
-            const uint32_t vm = otf_valid4(ctx, sd, Wq, n_here);
+            uint32_t vm = 0;
+            if (use_ci) {
+              const uint32_t *tab = reinterpret_cast<const uint32_t *>(ctx + 1);
+              uint32_t x = xci;
+              Wq[0] = W;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (u > 0) Wq[u] = otf_next_ci(ctx, Wq[u - 1], x);
+                if (u < n_here && ((tab[x >> 5] >> (x & 31)) & 1u)) vm |= 1u << u;
+              }
+            } else {
+              Wq[0] = W;
+#pragma unroll
+              for (int u = 1; u < 4; ++u) Wq[u] = otf_next(ctx, Wq[u - 1]);
+              vm = otf_valid4(ctx, sd, Wq, n_here);
+            }
             const uint32_t cnt = __popc(vm);
             const uint32_t incl = warp_incl(cnt);
             const uint32_t tot = __shfl_sync(FULL, incl, 31);
@@ -690,7 +739,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             lcount += (int)ktot;
             ord_base += tot;
             if (lcount >= kBatchE) walk_list(kBatchE);
-            W = otf_add128(ctx, W);
+            W = otf_add128(ctx, W, xci);
           }
         }
         if (lcount > 0) walk_list(lcount);

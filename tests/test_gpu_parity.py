@@ -276,8 +276,11 @@ def test_steps_topk(kt, name, K, depth, k):
     _check(out)
 
 
+# batch_6's constrained parameters have 270,336 value combinations, more than
+# the constrained-index table holds: it exercises the window-table check
 @pytest.mark.parametrize("name,select,k", [("tiny", "sample", 5), ("batch_3", "sample", 7),
-                                           ("batch_5", "topk", 16), ("batch_0", "topk", 5)])
+                                           ("batch_5", "topk", 16), ("batch_0", "topk", 5),
+                                           ("batch_6", "sample", 6), ("batch_6", "topk", 9)])
 def test_steps_on_the_fly(kt, name, select, k):
     d = W.space_tiny_block_tile() if name == "tiny" else W.load_space(name)
     roles = W.layout(32)
