@@ -465,12 +465,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int D = sd.D, L = 1 << D;
     const bool narrow = MODE != 1;
     const int tree_bytes = pack_tree_bytes(D, narrow);
+    // on the fly, only the node words are staged (the per-leaf terms are read
+    // from L2 once per walk): twice the trees per group, and every group costs
+    // a full decode pass of the raw range
+    const int stage_bytes = MODE == 2 ? 4 * L : tree_bytes;
     constexpr bool topk = TOPK;
     const int k = st.k;
     int budget = kBScoreSmem - (topk ? kTopkBytes : 0) - (MODE == 2 ? kOtfBytes + kCtxMax : 0);
-    const int per_group = max(1, budget / tree_bytes);
+    const int per_group = max(1, budget / stage_bytes);
     const int n_groups = max(1, (n_active + per_group - 1) / per_group);
-    uint8_t *tk_base = smem + (size_t)per_group * tree_bytes;
+    uint8_t *tk_base = smem + (size_t)per_group * stage_bytes;
     uint64_t *tk_key = reinterpret_cast<uint64_t *>(tk_base) + warp * KTUNE_MAX_K;
     int64_t *tk_raw = reinterpret_cast<int64_t *>(tk_base + kBWarps * KTUNE_MAX_K * 8) + warp * KTUNE_MAX_K;
     uint8_t *otf_base = tk_base + (topk ? kTopkBytes : 0);
@@ -524,10 +528,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int nt = max(0, min(per_group, n_active - t0));
       __syncthreads();
       {
-        const int per16 = tree_bytes / 16;
+        const int per16 = stage_bytes / 16;
         for (int a = 0; a < nt; ++a) {
           const uint4 *src = reinterpret_cast<const uint4 *>(sd.pack + (size_t)sh_active[t0 + a] * tree_bytes);
-          uint4 *dst = reinterpret_cast<uint4 *>(smem + (size_t)a * tree_bytes);
+          uint4 *dst = reinterpret_cast<uint4 *>(smem + (size_t)a * stage_bytes);
           for (int i = threadIdx.x; i < per16; i += blockDim.x) dst[i] = src[i];
         }
       }
@@ -542,11 +546,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int c = 0; c < CPT; ++c) s[c] = s_in[c];
         for (int a = 0; a < nt; ++a) {
-          const uint8_t *tb = smem + (size_t)a * tree_bytes;
+          const uint8_t *tb = smem + (size_t)a * stage_bytes;
           uint32_t j[CPT];
           if (narrow) {
             const uint32_t *words = reinterpret_cast<const uint32_t *>(tb);
-            const float *terms = reinterpret_cast<const float *>(tb + 4 * L);
+            const float *terms =
+                MODE == 2 ? reinterpret_cast<const float *>(sd.pack + (size_t)sh_active[t0 + a] * tree_bytes + 4 * L)
+                          : reinterpret_cast<const float *>(tb + 4 * L);
 #pragma unroll
             for (int c = 0; c < CPT; ++c) j[c] = 1u;
             for (int l = 0; l < D; ++l) {
@@ -554,7 +560,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], words[j[c]], Wv[c]);
             }
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) s[c] = __fadd_rn(s[c], terms[j[c] - (uint32_t)L]);
+            for (int c = 0; c < CPT; ++c)
+              s[c] = __fadd_rn(s[c], MODE == 2 ? __ldg(terms + (j[c] - (uint32_t)L)) : terms[j[c] - (uint32_t)L]);
           } else {
             const float *terms = reinterpret_cast<const float *>(tb + L);
 #pragma unroll
