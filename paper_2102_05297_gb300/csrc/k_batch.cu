@@ -528,12 +528,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int nt = max(0, min(per_group, n_active - t0));
       __syncthreads();
       {
+        // every thread issues all its 16-byte copies of the group's trees, then waits once
         const int per16 = stage_bytes / 16;
         for (int a = 0; a < nt; ++a) {
           const uint4 *src = reinterpret_cast<const uint4 *>(sd.pack + (size_t)sh_active[t0 + a] * tree_bytes);
           uint4 *dst = reinterpret_cast<uint4 *>(smem + (size_t)a * stage_bytes);
-          for (int i = threadIdx.x; i < per16; i += blockDim.x) dst[i] = src[i];
+          for (int i = threadIdx.x; i < per16; i += blockDim.x) cp_async16(dst + i, src + i);
         }
+        cp_async_wait_all();
       }
       __syncthreads();
       const bool first = g == 0, last = g == n_groups - 1;
@@ -793,25 +795,50 @@ __global__ void __launch_bounds__(256) k_bweights(const SearchDev *__restrict__ 
   __shared__ uint64_t part[kWSub][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t acc[kWSub];
+  // phase 1: every load of the CTA's sub-tiles (the stores of phase 2 could
+  // alias them, so issuing them first lets their latencies overlap)
+  const SearchDev *sdp[kWSub];
+  float4 sv[kWSub];
+  uint32_t evw[kWSub];
+  float mn[kWSub], mx[kWSub], gm[kWSub];
+  int64_t i0v[kWSub], Nv[kWSub];
+  bool live[kWSub];
+#pragma unroll
+  for (int u = 0; u < kWSub; ++u) {
+    const int64_t gs = blockIdx.x * (int64_t)kWSub + u;
+    live[u] = gs < n_sub_total;
+    sdp[u] = live[u] ? &srch[sub_search[gs]] : srch;
+  }
+#pragma unroll
+  for (int u = 0; u < kWSub; ++u) {
+    const SearchDev &sd = *sdp[u];
+    live[u] = live[u] && sd.select == KTUNE_SELECT_SAMPLE;
+    const int64_t gs = blockIdx.x * (int64_t)kWSub + u;
+    i0v[u] = (gs - sd.sub_begin) * kSubTile + (int64_t)threadIdx.x * 4;
+    Nv[u] = sd.N;
+    mn[u] = okey_inv(sd.mm[0]);
+    mx[u] = okey_inv(sd.mm[1]);
+    gm[u] = sd.gamma;
+    sv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    evw[u] = 0;
+    if (live[u] && i0v[u] + 3 < Nv[u]) {
+      sv[u] = *reinterpret_cast<const float4 *>(sd.s + i0v[u]);
+      evw[u] = sd.eval[i0v[u] >> 5] >> (i0v[u] & 31);
+    }
+  }
+  // phase 2: integer weights, their stores and sums
 #pragma unroll
   for (int u = 0; u < kWSub; ++u) {
     acc[u] = 0;
-    const int64_t gs = blockIdx.x * (int64_t)kWSub + u;
-    if (gs >= n_sub_total) continue;
-    const SearchDev &sd = srch[sub_search[gs]];
-    if (sd.select != KTUNE_SELECT_SAMPLE) continue;
-    const int64_t g = gs - sd.sub_begin;
-    const float mn = okey_inv(sd.mm[0]), mx = okey_inv(sd.mm[1]);
-    const int64_t N = sd.N;
-    const int64_t i0 = g * kSubTile + (int64_t)threadIdx.x * 4;   // four consecutive configurations
+    if (!live[u]) continue;
+    const SearchDev &sd = *sdp[u];
+    const int64_t i0 = i0v[u], N = Nv[u];
     if (i0 + 3 < N) {
-      const float4 sv = *reinterpret_cast<const float4 *>(sd.s + i0);
-      const uint32_t evw = sd.eval[i0 >> 5] >> (i0 & 31);
-      const float sa[4] = {sv.x, sv.y, sv.z, sv.w};
+      const float sa[4] = {sv[u].x, sv[u].y, sv[u].z, sv[u].w};
       uint32_t w[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        w[c] = ((evw >> c) & 1u) ? 0u : (uint32_t)weight_of(sa[c], mn, mx, sd.gamma);
+        w[c] = ((evw[u] >> c) & 1u) ? 0u : (uint32_t)weight_of(sa[c], mn[u], mx[u], gm[u]);
         acc[u] += w[c];
       }
       *reinterpret_cast<uint4 *>(sd.w + i0) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -819,7 +846,7 @@ __global__ void __launch_bounds__(256) k_bweights(const SearchDev *__restrict__ 
       for (int c = 0; c < 4; ++c) {
         const int64_t i = i0 + c;
         if (i < N) {
-          const uint32_t w = is_ev(sd.eval, i) ? 0u : (uint32_t)weight_of(sd.s[i], mn, mx, sd.gamma);
+          const uint32_t w = is_ev(sd.eval, i) ? 0u : (uint32_t)weight_of(sd.s[i], mn[u], mx[u], gm[u]);
           sd.w[i] = w;
           acc[u] += w;
         }
@@ -983,9 +1010,10 @@ __global__ void __launch_bounds__(kSelB) k_bselect(const SearchDev *__restrict__
     const int64_t n_super = (n_sub + kSuper - 1) / kSuper;
     const bool cached = n_sub <= kSubCache;
     uint64_t *subs = cached ? sub_c : sd.sub_sum;
-    for (int64_t sp = threadIdx.x; sp < n_super; sp += blockDim.x) super_sum[sp] = sd.super_sum[sp];
+    for (int64_t sp = threadIdx.x; sp < n_super; sp += blockDim.x) cp_async8(super_sum + sp, sd.super_sum + sp);
     if (cached)
-      for (int64_t g = threadIdx.x; g < n_sub; g += blockDim.x) sub_c[g] = sd.sub_sum[g];
+      for (int64_t g = threadIdx.x; g < n_sub; g += blockDim.x) cp_async8(sub_c + g, sd.sub_sum + g);
+    cp_async_wait_all();
     __syncthreads();
     if (warp == 0) {
       // descriptor fields in registers: the loop's stores cannot alias them
