@@ -16,7 +16,9 @@ The per-step inputs (the measured counters of each step's c_profile) come
 from a recorded search over the synthetic performance function; the timed
 steps replay them from device memory (``value``), and the end-to-end leg
 replays them through the host API with its copies (``e2e``).  L2 is flushed
-between timed steps (a 256 MB write outside the timed region).
+between timed steps (a 512 MB write outside the timed region, queued before
+the step so that the device-timed region excludes host launch latency, which
+``e2e`` includes).
 
 ``paths`` (same JSON line) measures the other forms of the step, each with
 the roofline of its dominant kernel:
@@ -86,7 +88,7 @@ def describe(name, wl, desc, n_valid):
                             100 * wl["frac"], 100 * wl["noise"], wl["k"]),
             "n_valid": int(n_valid), "n_raw": int(desc.n_raw), "K": wl["K"],
             "depth": wl["depth"], "k": wl["k"], "select": "sample",
-            "l2": "flushed between timed steps (256 MB write outside the timed region)"}
+            "l2": "flushed between timed steps (512 MB write outside the timed region)"}
 
 
 def alu_peak(props, pk):
@@ -247,7 +249,10 @@ def run_ours(args):
     # a dedicated stream: steps on a non-default stream run as one captured CUDA graph
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    # written before every timed step: larger than L2, and long enough (~80 us)
+    # that the step's host-side enqueue finishes before the device reaches the
+    # step's start event, so the events bracket device work only
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     # ---- device-resident timed steps -------------------------------------
     bufs = (torch.empty(wl["k"], dtype=torch.int64, device="cuda").data_ptr(),

@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(256) k_bprep(const SearchDev *__restrict__ src
                                                const __grid_constant__ StepBatch<NB> sb) {
   extern __shared__ __align__(16) uint8_t tree_sm[];   // node bytes of tree p (2^D)
   __shared__ float sh_pc;
+  pdl_wait();
+  pdl_launch_dependents();
   const SearchDev &sd = srch[blockIdx.z];
   const StepDev &st = sb.st[blockIdx.z];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) steps_dev[blockIdx.z] = st;
@@ -431,6 +433,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_bscore(const SearchDev *__restrict__ srch, const StepDev *__restrict__ steps,
              const ItemDev *__restrict__ items, int n_items) {
   extern __shared__ __align__(16) uint8_t smem[];
+  pdl_wait();                 // the prepare kernel's Delta, c_profile and term tables
+  pdl_launch_dependents();
   constexpr int kBThreads = THREADS;
   constexpr int kBWarps = THREADS / 32;
   constexpr int kTopkBytes = kBWarps * KTUNE_MAX_K * 16;   // per-warp lists (key + raw)
@@ -789,10 +793,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ---- weights -----------------------------------------------------------------------------
 constexpr int kWSub = 4;   // sub-tiles per weights CTA
 
-__global__ void __launch_bounds__(256) k_bweights(const SearchDev *__restrict__ srch,
+// (256, 4): at most 64 registers, so the whole grid of a mid-size space is one wave
+__global__ void __launch_bounds__(256, 4) k_bweights(const SearchDev *__restrict__ srch,
                                                   const int *__restrict__ sub_search,
                                                   int64_t n_sub_total) {
   __shared__ uint64_t part[kWSub][8];
+  pdl_wait();                 // the scores, minimum and maximum
+  pdl_launch_dependents();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t acc[kWSub];
   // phase 1: every load of the CTA's sub-tiles (the stores of phase 2 could
@@ -938,6 +945,8 @@ constexpr int kSubCache = 4096;   // sub-tile sums held in shared memory when th
 __global__ void __launch_bounds__(kSelB) k_bselect(const SearchDev *__restrict__ srch,
                                                   const StepDev *__restrict__ steps) {
   extern __shared__ __align__(16) uint64_t sel_sm[];
+  pdl_wait();                 // the weights and their tile sums (or the top-k candidates)
+  pdl_launch_dependents();
   uint64_t *super_sum = sel_sm;                   // [kMaxSuper]
   uint64_t *sub_c = sel_sm + kMaxSuper;           // [kSubCache]
   __shared__ uint64_t sh64[32];
@@ -1025,13 +1034,17 @@ __global__ void __launch_bounds__(kSelB) k_bselect(const SearchDev *__restrict__
       const uint32_t sid = sd.search_id, stp = st.step;
       const int64_t per = (n_super + 31) / 32;
       const int64_t slo = min(n_super, per * lane), shi = min(n_super, slo + per);
+      // the draws' Philox variates, one lane each, before the serial loop
+      const uint64_t u_lo = philox_u64(seed, sid, stp, (uint32_t)lane, 0u);
+      const uint64_t u_hi = lane + 32 < k ? philox_u64(seed, sid, stp, (uint32_t)(lane + 32), 0u) : 0ull;
       for (int j = 0; j < k; ++j) {
         uint64_t local = 0;
         for (int64_t sp = slo; sp < shi; ++sp) local += super_sum[sp];
         const uint64_t incl = warp_incl(local);
         const uint64_t W = __shfl_sync(FULL, incl, 31);
         if (W == 0) break;
-        const uint64_t r = scaled_draw(philox_u64(seed, sid, stp, (uint32_t)j, 0u), W);
+        const uint64_t uj = j < 32 ? __shfl_sync(FULL, u_lo, j) : __shfl_sync(FULL, u_hi, j - 32);
+        const uint64_t r = scaled_draw(uj, W);
         // super-tile holding r
         int64_t sp_sel = -1;
         uint64_t r1 = 0;
@@ -1079,9 +1092,15 @@ __global__ void __launch_bounds__(kSelB) k_bselect(const SearchDev *__restrict__
 #pragma unroll
           for (int q = 0; q < 32; ++q) wv[q] = i0 + q < N ? __ldcg(wp + i0 + q) : 0u;
         }
-        uint64_t ls = 0;
+        // the lane's sum as a tree of adds (depth 5, not a chain of 32)
+        uint64_t t16[16];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) ls += wv[q];
+        for (int q = 0; q < 16; ++q) t16[q] = (uint64_t)wv[2 * q] + wv[2 * q + 1];
+#pragma unroll
+        for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+          for (int q = 0; q < w; ++q) t16[q] = t16[2 * q] + t16[2 * q + 1];
+        const uint64_t ls = t16[0];
         const uint64_t inc3 = warp_incl(ls);
         const bool mine = inc3 - ls <= r2 && r2 < inc3;
         uint64_t acc = inc3 - ls;
@@ -1181,6 +1200,25 @@ int bscore_variants() { return kNumVariants; }
 int bscore_variant_threads(int v) { return kVariants[v].threads; }
 int bscore_variant_cpt(int v) { return kVariants[v].cpt; }
 
+// Launch on `st`; on a non-default stream the kernel may be scheduled while
+// its predecessor finishes (programmatic dependent launch), and waits for it
+// in pdl_wait() before touching its results.
+template <typename... KArgs, typename... Args>
+static void launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = st != nullptr ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <int THREADS, int CPT, int MODE, bool TOPK>
 static void launch_one(const SearchDev *srch, const StepDev *steps, const ItemDev *items,
                        int n_items, int grid, cudaStream_t st) {
@@ -1190,7 +1228,8 @@ static void launch_one(const SearchDev *srch, const StepDev *steps, const ItemDe
                          cudaFuncAttributeMaxDynamicSharedMemorySize, kBScoreSmem);
     attr = true;
   }
-  k_bscore<THREADS, CPT, MODE, TOPK><<<grid, THREADS, kBScoreSmem, st>>>(srch, steps, items, n_items);
+  launch_dep(k_bscore<THREADS, CPT, MODE, TOPK>, dim3(grid), dim3(THREADS), kBScoreSmem, st, srch,
+             steps, items, n_items);
 }
 
 template <int MODE, bool TOPK>
@@ -1227,8 +1266,8 @@ void launch_bscore(const SearchDev *srch, const StepDev *steps, const ItemDev *i
 void launch_bweights(const SearchDev *srch, const int *sub_search, int64_t n_sub_total,
                      cudaStream_t st) {
   static_assert(kSubTile == 256 * 4, "256 threads x 4 configurations per sub-tile");
-  k_bweights<<<(unsigned)((n_sub_total + kWSub - 1) / kWSub), 256, 0, st>>>(srch, sub_search,
-                                                                           n_sub_total);
+  launch_dep(k_bweights, dim3((unsigned)((n_sub_total + kWSub - 1) / kWSub)), dim3(256), 0, st, srch,
+             sub_search, n_sub_total);
 }
 
 void launch_bselect(const SearchDev *srch, const StepDev *steps, int S, cudaStream_t st) {
@@ -1238,7 +1277,7 @@ void launch_bselect(const SearchDev *srch, const StepDev *steps, int S, cudaStre
     cudaFuncSetAttribute(k_bselect, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  k_bselect<<<S, kSelB, smem, st>>>(srch, steps);
+  launch_dep(k_bselect, dim3(S), dim3(kSelB), smem, st, srch, steps);
 }
 
 }  // namespace ktune
