@@ -62,7 +62,14 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
-ALL_PATHS = ("mlp", "batch", "large", "tiny")
+ALL_PATHS = ("mlp", "cached", "batch", "large", "tiny")
+# DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
+# captures summarised under profiles/ (the kernels have not changed since)
+PROFILED_TRAFFIC = {
+    "k_bscore": 9.633e6,          # profiles/k_bscore_mid_12p.md
+    "k_mlp_pipe": 18.809e6,       # profiles/k_mlp_pipe_mid_12p.md
+    "k_bscore_otf": 20.228e6,     # profiles/k_bscore_otf_large_16p.md
+}
 MLP_HIDDEN = 256
 
 
@@ -313,6 +320,8 @@ def run_ours(args):
         if "mlp" in want:
             paths["mlp"] = path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, m, samp, traj,
                                     tree_ms=1e3 * t_total / K)
+        if "cached" in want:
+            paths["cached"] = path_cached(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "batch" in want:
             paths["batch"] = path_batch(ctx)
         if "large" in want:
@@ -350,7 +359,8 @@ def run_ours(args):
             "peak": peak_visits / 1e9,
             "unit": "Gvisit/s",
             "frac": achieved / peak_visits,
-            "traffic": None,
+            "traffic": PROFILED_TRAFFIC["k_bscore"],
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
             "peak_source": "derived: %d SMs x 4 SMSPs x 32 lanes x %.0f MHz (%s sm_max) / 4 "
                            "instructions per node visit" % (props.multi_processor_count, sm_mhz, src),
             "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(), "score": kern_ms[1] / kern_ms.sum(),
@@ -429,6 +439,16 @@ def path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp
                                                         min(len(traj), Wu + n_steps), wl["k"],
                                                         stream, flush)
     s.close()
+    # the same search with cached predictions (the network predicts TS once)
+    sc = kt.Search(sp, model, k=wl["k"], seed=0, stream=stream)
+    torch.cuda.synchronize()
+    tf = time.perf_counter()
+    sc.set_cached(True)
+    fill_ms = 1e3 * (time.perf_counter() - tf)
+    untimed_device_steps(sc, traj, 0, Wu, wl["k"], bufs, stream)
+    c_ms, _, _, c_scored, _ = timed_device_steps(kt, torch, sc, traj, Wu,
+                                                 min(len(traj), Wu + n_steps), wl["k"], stream, flush)
+    sc.close()
     model.close()
     mlp.close()
     t = sum(step_ms) / 1e3
@@ -448,14 +468,67 @@ def path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp
                                        "sample (%d configurations) against the noise-free synthetic "
                                        "counters; trees: depth 12 on a 2%% sample" % (Kc, len(held))},
         "speedup_vs_tree": tree_ms / (1e3 * t / ns),
+        "cached": {"ms_per_step": sum(c_ms) / len(c_ms), "fill_ms": fill_ms,
+                   "value": c_scored / (sum(c_ms) / 1e3), "unit": "configs/s",
+                   "speedup_vs_tree_fused": tree_ms / (sum(c_ms) / len(c_ms))},
         "train": {"ms": train_ms, "final_loss": float(losses[-1]), "first_loss": float(losses[0]),
                   "tflops": train_flops / (train_ms / 1e3) / 1e12,
                   "flops": "3 x forward (%d FLOP per row) per row" % fpc},
         "roofline": {"bound": "tensor", "kernel": "k_mlp_fwd<score> (fused forward + Eq. score)",
                      "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                     "frac": ach / peak, "traffic": None,
+                     "frac": ach / peak, "traffic": PROFILED_TRAFFIC["k_mlp_pipe"],
                      "peak_source": "%s bf16 burst (cuBLAS GEMM)" % ctx["src"],
                      "flop_per_config": fpc,
+                     "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
+                                      "score": kern_ms[1] / kern_ms.sum(),
+                                      "weights": kern_ms[2] / kern_ms.sum(),
+                                      "select": kern_ms[3] / kern_ms.sum()}},
+    }
+
+
+def path_cached(ctx, wl, sp, m, traj, fused_ms):
+    """The headline search with cached predictions: the trees predict all of TS
+    once; each step streams the active counters' columns (HBM-bound)."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    Wu, n_steps = ctx["warmup"], ctx["steps"]
+    k = wl["k"]
+    bufs = (torch.empty(k, dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(k, dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = kt.Search(sp, m, k=k, seed=0, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_cached(True)
+    fill_ms = 1e3 * (time.perf_counter() - t0)
+    untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+    step_ms, _, _, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + n_steps, k, stream,
+                                                  flush)
+    s.close()
+    s = kt.Search(sp, m, k=k, seed=0, stream=stream)
+    s.set_cached(True)
+    s.set_timing(True)
+    untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+    _, kern_ms, _, _, nact = timed_device_steps(kt, torch, s, traj, Wu, Wu + n_steps, k, stream, flush)
+    s.close()
+    t = sum(step_ms) / 1e3
+    ns = len(step_ms)
+    # algorithmic bytes: 4 per active counter column read, 4 per score written,
+    # 1/8 per evaluated bit, per scored configuration
+    bytes_ = sum(float(scored) / ns * (4.0 * a + 4.125) for a in nact)
+    ach = bytes_ / (kern_ms[1] / 1e3)
+    peak = float(ctx["pk"].get("hbm_gbs", 6800.0)) * 1e9
+    return {
+        "workload": "the headline search with cached predictions (depth-12 trees predict all "
+                    "%d configurations once; each step streams the active counters' columns)"
+                    % (scored // ns),
+        "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / ns,
+        "steps_per_s": ns / t, "steps": ns, "fill_ms": fill_ms,
+        "speedup_vs_fused": fused_ms / (1e3 * t / ns),
+        "roofline": {"bound": "hbm", "kernel": "k_cscore (Eq. score from cached columns)",
+                     "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "peak_source": "%s STREAM-style copy" % ctx["src"],
+                     "bytes_per_config": "4 x active counters (mean %.2f) + 4.125" % np.mean(nact),
                      "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
                                       "score": kern_ms[1] / kern_ms.sum(),
                                       "weights": kern_ms[2] / kern_ms.sum(),
@@ -644,7 +717,7 @@ def path_large(ctx, depth=12):
         "raw_decoded_per_s": n_raw * n_steps / t,
         "roofline": {"bound": "alu", "kernel": "k_bscore<on-the-fly> (decode + filter + walk + score)",
                      "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "Gvisit/s",
-                     "frac": ach / peak, "traffic": None,
+                     "frac": ach / peak, "traffic": PROFILED_TRAFFIC["k_bscore_otf"],
                      "mean_active_counters": float(np.mean(nact)),
                      "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
                                       "score": kern_ms[1] / kern_ms.sum(),

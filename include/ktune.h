@@ -235,6 +235,20 @@ int ktune_search_save(const ktune_search *search, void *buf, size_t *bytes);
 int ktune_search_load(ktune_space *space, ktune_model *model, const void *buf, size_t bytes,
                       void *stream, ktune_search **out);
 
+/* Cached predictions (no counterpart in the paper; the model and the space
+ * do not change between steps, so neither do the predictions).  enable = 1
+ * predicts every configuration of TS with the search's model now, into a
+ * device array the search owns (K float32 per configuration, one column per
+ * counter: K x ceil(N/4)*4 floats); later ktune_step / ktune_step_device
+ * calls then compute Eq. score from the columns of the counters with a
+ * non-zero Delta and c_profile prediction instead of predicting again, with
+ * the same scores and selections (the same float32 terms, summed in the same
+ * order).  Call again after the model changed (for example after further MLP
+ * training); enable = 0 frees the array.  Needs a materialised space and
+ * KTUNE_SELECT_SAMPLE (KTUNE_ESTATE otherwise).  Batched steps do not use
+ * the cache.  Synchronises the search's stream. */
+int ktune_search_set_cached(ktune_search *search, int enable);
+
 /* Statistics of the most recent step.  kernel_ms holds the device time of
  * each kernel of that step in launch order (prepare, score, weights, select),
  * measured with CUDA events on the step's stream, only while timing is

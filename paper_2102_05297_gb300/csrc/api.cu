@@ -941,6 +941,7 @@ static void drop_graph(ktune_search *h) {
 }
 
 int ktune_search_destroy(ktune_search *h) {
+  if (h) cudaFree(h->d_cache);
   if (!h) return KTUNE_OK;
   void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
                  h->d_s, h->d_w, h->d_subsum, h->d_supsum, h->d_cand_key, h->d_cand_raw, h->d_mm, h->d_srch,
@@ -990,7 +991,19 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
     else cudaEventRecord(h->ev[i], st);
   };
   mark(0);
-  if (m->kind == 2) {
+  if (h->cached) {
+    // cached predictions: the step's set-up and c_profile prediction, then
+    // Eq. score from the cached columns of the active counters
+    if (m->kind == 2) {
+      launch_mlp_prep(h->d_srch, h->d_steps, sb, st);
+      launch_mlp_fwd(0, m->mlp->dev(), &h->d_steps[0].cprof_packed, 1, h->d_pcprof, nullptr,
+                     nullptr, nullptr, nullptr, m->mlp->d_status, 1, st);
+    } else {
+      launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
+    }
+    mark(1);
+    launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
+  } else if (m->kind == 2) {
     // MLP: set-up, prediction of c_profile, then predict + score all of TS
     const MlpDev md = m->mlp->dev();
     launch_mlp_prep(h->d_srch, h->d_steps, sb, st);
@@ -1237,6 +1250,57 @@ int ktune_search_load(ktune_space *s, ktune_model *m, const void *buf, size_t by
   h->n_evaluated = hd.n_evaluated;
   h->step_no = hd.step_no;
   *out = h;
+  return KTUNE_OK;
+}
+
+int ktune_search_set_cached(ktune_search *h, int enable) {
+  if (!h) FAIL(KTUNE_EINVAL, "null search");
+  if (!enable) {
+    if (h->cached || h->d_cache) {
+      CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : h->stream));
+      cudaFree(h->d_cache);
+      h->d_cache = nullptr;
+      h->cached = false;
+      drop_graph(h);
+    }
+    return KTUNE_OK;
+  }
+  const ktune_space *s = h->space;
+  if (!s->d_packed) FAIL(KTUNE_ESTATE, "cached predictions need a materialised space");
+  if (h->opts.select != KTUNE_SELECT_SAMPLE) FAIL(KTUNE_ESTATE, "cached predictions need weighted-draw selection");
+  const int K = h->model->K;
+  const int64_t N = s->n_valid, Np = (N + 3) & ~(int64_t)3;
+  cudaStream_t st = h->stream;
+  CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : st));
+  if (!h->d_cache) {
+    int rc = dalloc(&h->d_cache, (size_t)K * Np);
+    if (rc) return rc;
+    h->cache_np = Np;
+  }
+  // predictions in chunks of rows, each transposed into the columns
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(N, (int64_t)(16 << 20) / K));
+  float *rows = nullptr;
+  int rc = dalloc(&rows, (size_t)chunk * K);
+  if (rc) return rc;
+  for (int64_t first = 0; first < N && rc == KTUNE_OK; first += chunk) {
+    const int64_t n = std::min<int64_t>(chunk, N - first);
+    rc = ktune_model_predict_device(h->model, first, n, rows, st);
+    if (rc == KTUNE_OK) launch_rows_to_cols(rows, n, K, h->d_cache, Np, first, st);
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(rows);
+  if (rc) return rc;
+  if (e != cudaSuccess) FAIL(KTUNE_ECUDA, std::string("cache fill: ") + cudaGetErrorString(e));
+  if (h->model->kind == 2) {
+    int status = 0;
+    CK(cudaMemcpy(&status, h->model->mlp->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+      cudaMemset(h->model->mlp->d_status, 0, sizeof(int));
+      FAIL(KTUNE_ETIMEOUT, "a tensor-core wait of the MLP timed out");
+    }
+  }
+  h->cached = true;
+  drop_graph(h);
   return KTUNE_OK;
 }
 

@@ -252,6 +252,11 @@ struct MlpTargets {
 void launch_mlp_score_shared(const MlpDev &md, const uint64_t *packed, int64_t n,
                              const MlpTargets &tg, int *status, int max_ctas, cudaStream_t st);
 
+// cached predictions (k_cache.cu)
+void launch_rows_to_cols(const float *rows, int64_t n, int K, float *cache, int64_t Np, int64_t first,
+                         cudaStream_t st);
+void launch_cscore(const SearchDev *srch, const float *cache, int64_t Np, int num_sms, cudaStream_t st);
+
 int mlp_fwd_smem(int F);
 bool mlp_pipe_supported(int F);
 void mlp_pipe_set_attrs();
@@ -410,6 +415,10 @@ struct ktune_search {
   bool use_graph = true;
   std::vector<int64_t> last_raw;
   std::vector<uint64_t> last_packed;
+  // cached predictions: K columns of Np floats (Np = N rounded up to 4)
+  float *d_cache = nullptr;
+  int64_t cache_np = 0;
+  bool cached = false;
   // device buffers
   uint32_t *d_eval = nullptr;
   float *d_counters = nullptr, *d_pcprof = nullptr, *d_delta = nullptr;
