@@ -545,9 +545,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool first = g == 0, last = g == n_groups - 1;
 
       // walk CPT configurations per thread; inputs/outputs through lambdas
+      // evb: per configuration its evaluated bit when already loaded (bit 1 of
+      // evb[c] set), else looked up here
       auto walk_and_finish = [&](const uint32_t (&Wv)[CPT], const uint64_t (&Pv)[CPT],
                                  const int64_t (&ordv)[CPT], const int64_t (&rawv)[CPT],
-                                 const bool (&ok)[CPT], const float (&s_in)[CPT]) {
+                                 const bool (&ok)[CPT], const float (&s_in)[CPT],
+                                 const uint32_t (&evb)[CPT]) {
         float s[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) s[c] = s_in[c];
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (ok[c]) s_p[ordv[c]] = s[c];
             continue;
           }
-          const bool ev = ok[c] && is_ev(eval_p, ordv[c]);
+          const bool ev = ok[c] && ((evb[c] & 2u) ? (evb[c] & 1u) != 0u : is_ev(eval_p, ordv[c]));
           if (ok[c]) s_p[ordv[c]] = ev ? 0.0f : s[c];
           const bool live = ok[c] && !ev;
           if (live) {
@@ -606,6 +609,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t Wn[CPT];
         uint64_t Pn[CPT];
         float sn[CPT];
+        uint32_t en[CPT];
         auto load = [&](int64_t base) {
 #pragma unroll
           for (int c = 0; c < CPT; ++c) {
@@ -614,6 +618,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             Wn[c] = (MODE == 0 && in) ? __ldg(narrow_p + i) : 0u;
             Pn[c] = (in && (MODE == 1 || topk)) ? __ldg(packed_p + i) : 0ull;
             sn[c] = (first || !in) ? 0.0f : s_p[i];
+            // the evaluated bit, loaded with the chunk in the last group (2 = loaded)
+            en[c] = (last && in) ? (2u | ((__ldg(eval_p + (i >> 5)) >> (i & 31)) & 1u)) : 0u;
           }
         };
         load(it.lo);
@@ -623,6 +629,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           float s_in[CPT];
           int64_t ordv[CPT], rawv[CPT];
           bool ok[CPT];
+          uint32_t evb[CPT];
 #pragma unroll
           for (int c = 0; c < CPT; ++c) {
             const int64_t i = base + (int64_t)c * kBThreads + threadIdx.x;
@@ -631,6 +638,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             Wv[c] = Wn[c];
             Pv[c] = Pn[c];
             s_in[c] = sn[c];
+            evb[c] = en[c];
             rawv[c] = 0;
             if (topk && ok[c]) {
               int64_t r = 0;
@@ -639,7 +647,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
           if (base + kStep < it.hi) load(base + kStep);
-          walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in);
+          walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in, evb);
         }
       } else {
         // on-the-fly: every warp decodes whole raw tiles by itself.  Lane l
@@ -683,7 +691,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           __syncwarp();
           lcount = rem;
-          walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in);
+          // the list holds unevaluated configurations only
+          uint32_t evb[CPT];
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) evb[c] = 2u;
+          walk_and_finish(Wv, Pv, ordv, rawv, ok, s_in, evb);
         };
         for (int64_t t = it.lo + warp; t < it.hi; t += kBWarps) {
           const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
