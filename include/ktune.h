@@ -238,12 +238,14 @@ int ktune_search_load(ktune_space *space, ktune_model *model, const void *buf, s
 /* Cached predictions (no counterpart in the paper; the model and the space
  * do not change between steps, so neither do the predictions).  enable = 1
  * predicts every configuration of TS with the search's model now, into a
- * device array the search owns (K float32 per configuration, one column per
- * counter: K x ceil(N/4)*4 floats); later ktune_step / ktune_step_device
- * calls then compute Eq. score from the columns of the counters with a
- * non-zero Delta and c_profile prediction instead of predicting again, with
- * the same scores and selections (the same float32 terms, summed in the same
- * order).  Call again after the model changed (for example after further MLP
+ * device array the search owns, one column per counter of ceil(N/8)*8
+ * entries: for a tree model the leaf each configuration reaches (uint16), for
+ * the MLP the predicted counter (float32); later ktune_step /
+ * ktune_step_device calls then compute Eq. score from the columns of the
+ * counters with a non-zero Delta and c_profile prediction (trees: the step's
+ * per-leaf terms indexed by the cached leaves) instead of predicting again,
+ * with the same scores and selections (the same float32 terms, summed in the
+ * same order).  Call again after the model changed (for example after further MLP
  * training); enable = 0 frees the array.  Needs a materialised space and
  * KTUNE_SELECT_SAMPLE (KTUNE_ESTATE otherwise).  Batched steps do not use
  * the cache.  Synchronises the search's stream. */

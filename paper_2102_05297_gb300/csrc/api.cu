@@ -941,8 +941,9 @@ static void drop_graph(ktune_search *h) {
 }
 
 int ktune_search_destroy(ktune_search *h) {
-  if (h) cudaFree(h->d_cache);
   if (!h) return KTUNE_OK;
+  cudaFree(h->d_cache);
+  cudaFree(h->d_leaf_cache);
   void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
                  h->d_s, h->d_w, h->d_subsum, h->d_supsum, h->d_cand_key, h->d_cand_raw, h->d_mm, h->d_srch,
                  h->d_steps, h->d_items, h->d_sub_search, h->d_out_raw, h->d_out_score,
@@ -998,11 +999,16 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
       launch_mlp_prep(h->d_srch, h->d_steps, sb, st);
       launch_mlp_fwd(0, m->mlp->dev(), &h->d_steps[0].cprof_packed, 1, h->d_pcprof, nullptr,
                      nullptr, nullptr, nullptr, m->mlp->d_status, 1, st);
+      mark(1);
+      launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
     } else {
       launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
+      mark(1);
+      const bool narrow = h->mode != 1;
+      const int L = 1 << m->D;
+      launch_cscore_leaf(h->d_srch, h->d_leaf_cache, h->cache_np, pack_tree_bytes(m->D, narrow),
+                         narrow ? 4 * L : L, h->num_sms, st);
     }
-    mark(1);
-    launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
   } else if (m->kind == 2) {
     // MLP: set-up, prediction of c_profile, then predict + score all of TS
     const MlpDev md = m->mlp->dev();
@@ -1256,10 +1262,12 @@ int ktune_search_load(ktune_space *s, ktune_model *m, const void *buf, size_t by
 int ktune_search_set_cached(ktune_search *h, int enable) {
   if (!h) FAIL(KTUNE_EINVAL, "null search");
   if (!enable) {
-    if (h->cached || h->d_cache) {
+    if (h->cached || h->d_cache || h->d_leaf_cache) {
       CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : h->stream));
       cudaFree(h->d_cache);
+      cudaFree(h->d_leaf_cache);
       h->d_cache = nullptr;
+      h->d_leaf_cache = nullptr;
       h->cached = false;
       drop_graph(h);
     }
@@ -1269,9 +1277,22 @@ int ktune_search_set_cached(ktune_search *h, int enable) {
   if (!s->d_packed) FAIL(KTUNE_ESTATE, "cached predictions need a materialised space");
   if (h->opts.select != KTUNE_SELECT_SAMPLE) FAIL(KTUNE_ESTATE, "cached predictions need weighted-draw selection");
   const int K = h->model->K;
-  const int64_t N = s->n_valid, Np = (N + 3) & ~(int64_t)3;
+  const int64_t N = s->n_valid, Np = (N + 7) & ~(int64_t)7;
   cudaStream_t st = h->stream;
   CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : st));
+  if (h->model->kind == 1) {   // trees: the leaf index of every configuration in every tree
+    if (!h->d_leaf_cache) {
+      int rc = dalloc(&h->d_leaf_cache, (size_t)K * Np);
+      if (rc) return rc;
+      h->cache_np = Np;
+    }
+    launch_leaf_cols(s->d_packed, N, h->model->d_nodes, K, h->model->D, h->d_leaf_cache, Np, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) FAIL(KTUNE_ECUDA, std::string("cache fill: ") + cudaGetErrorString(e));
+    h->cached = true;
+    drop_graph(h);
+    return KTUNE_OK;
+  }
   if (!h->d_cache) {
     int rc = dalloc(&h->d_cache, (size_t)K * Np);
     if (rc) return rc;

@@ -256,6 +256,10 @@ void launch_mlp_score_shared(const MlpDev &md, const uint64_t *packed, int64_t n
 void launch_rows_to_cols(const float *rows, int64_t n, int K, float *cache, int64_t Np, int64_t first,
                          cudaStream_t st);
 void launch_cscore(const SearchDev *srch, const float *cache, int64_t Np, int num_sms, cudaStream_t st);
+void launch_leaf_cols(const uint64_t *packed, int64_t N, const uint8_t *nodes, int K, int D,
+                      uint16_t *out, int64_t Np, cudaStream_t st);
+void launch_cscore_leaf(const SearchDev *srch, const uint16_t *leaves, int64_t Np, int tree_bytes,
+                        int terms_off, int num_sms, cudaStream_t st);
 
 int mlp_fwd_smem(int F);
 bool mlp_pipe_supported(int F);
@@ -415,8 +419,10 @@ struct ktune_search {
   bool use_graph = true;
   std::vector<int64_t> last_raw;
   std::vector<uint64_t> last_packed;
-  // cached predictions: K columns of Np floats (Np = N rounded up to 4)
+  // cached predictions: K columns of Np floats (MLP) or Np uint16 leaf indices
+  // (trees); Np = N rounded up to 8
   float *d_cache = nullptr;
+  uint16_t *d_leaf_cache = nullptr;
   int64_t cache_np = 0;
   bool cached = false;
   // device buffers
