@@ -66,7 +66,8 @@ ALL_PATHS = ("mlp", "cached", "batch", "large", "tiny")
 # DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
 # captures summarised under profiles/ (the kernels have not changed since)
 PROFILED_TRAFFIC = {
-    "k_bscore": None,             # changed since profiles/k_bscore_mid_12p.md (9.633e6 then)
+    "k_bscore": 9.637e6,          # profiles/k_bscore_mid_12p.md
+    "k_cscore_leaf": 36.564e6,    # profiles/cached_mid_12p.md
     "k_mlp_pipe": 18.809e6,       # profiles/k_mlp_pipe_mid_12p.md
     "k_bscore_otf": 20.228e6,     # profiles/k_bscore_otf_large_16p.md
 }
@@ -528,7 +529,8 @@ def path_cached(ctx, wl, sp, m, traj, fused_ms):
         "speedup_vs_fused": fused_ms / (1e3 * t / ns),
         "roofline": {"bound": "hbm", "kernel": "k_cscore_leaf (Eq. score from cached leaf indices)",
                      "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": ach / peak,
-                     "traffic": None, "peak_source": "%s STREAM-style copy" % ctx["src"],
+                     "traffic": PROFILED_TRAFFIC["k_cscore_leaf"],
+                     "peak_source": "%s STREAM-style copy" % ctx["src"],
                      "bytes_per_config": "2 x active counters (mean %.2f) + 4.125" % np.mean(nact),
                      "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
                                       "score": kern_ms[1] / kern_ms.sum(),
