@@ -317,7 +317,8 @@ int ktune_batch_variant(int v, int *threads, int *cpt, int *items_per_cta);
 typedef struct ktune_mlp ktune_mlp;
 /* roles: HOST int32[K] (KTUNE_PC_*), ranges: HOST float[K] > 0 (finite);
  * max_batch: largest training batch, a multiple of 16 in 16..65536.
- * Parameters start at zero and the Adam state empty.  Requires F <= 384. */
+ * Parameters start at zero and the Adam state empty.  Requires F <= 256 (every
+ * space within the limits of ktune_space_create satisfies it). */
 int ktune_mlp_create(ktune_space *s, int K, const int32_t *roles, const float *ranges,
                      int max_batch, void *stream, ktune_mlp **out);
 int ktune_mlp_destroy(ktune_mlp *m);

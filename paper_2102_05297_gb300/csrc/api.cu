@@ -1489,15 +1489,8 @@ void batch_launch(ktune_batch *b, const StepBatch<kMaxBatch> &sb, cudaStream_t s
     const int S = (int)g.members.size();
     launch_mlp_fwd(0, md, g.d_cprof, S, g.d_pcprof, nullptr, nullptr, nullptr, nullptr,
                    h->model->mlp->d_status, 1, st);
-    if (mlp_pipe_supported(md.F) && md.wc)
-      launch_mlp_score_shared(md, h->space->d_packed, h->space->n_valid, g.tg,
-                              h->model->mlp->d_status, b->num_sms, st);
-    else
-      for (int q = 0; q < S; ++q) {
-        ktune_search *m = b->s[g.members[q]];
-        launch_mlp_fwd(1, md, h->space->d_packed, h->space->n_valid, m->d_s, g.tg.pcprof[q],
-                       m->d_delta, m->d_eval, m->d_mm, h->model->mlp->d_status, b->num_sms, st);
-      }
+    launch_mlp_score_shared(md, h->space->d_packed, h->space->n_valid, g.tg,
+                            h->model->mlp->d_status, b->num_sms, st);
   }
   if (!b->topk) launch_bweights(b->d_srch, b->d_sub_search, b->n_sub, st);
   launch_bselect(b->d_srch, b->d_steps, S, st);

@@ -205,7 +205,7 @@ void launch_mark(uint32_t *evaluated, int64_t ordinal, cudaStream_t st);
 
 // ---- MLP counter model (k_mlp.cu) ----
 constexpr int kMlpHidden = 256;
-constexpr int kMlpMaxF = 384;           // feature columns (multiple of 16)
+constexpr int kMlpMaxF = 256;           // feature columns (multiple of 16)
 // weights of the pipelined forward: chunks of kMlpChunkK K-columns in the
 // shared-memory operand layout, streamed through kMlpStages stages
 constexpr int kMlpChunkK = 32;
@@ -261,7 +261,6 @@ void launch_leaf_cols(const uint64_t *packed, int64_t N, const uint8_t *nodes, i
 void launch_cscore_leaf(const SearchDev *srch, const uint16_t *leaves, int64_t Np, int tree_bytes,
                         int terms_off, int num_sms, cudaStream_t st);
 
-int mlp_fwd_smem(int F);
 bool mlp_pipe_supported(int F);
 void mlp_pipe_set_attrs();
 void launch_pack_wc(const uint16_t *w, int Nl, int Kl, uint8_t *dst, cudaStream_t st);

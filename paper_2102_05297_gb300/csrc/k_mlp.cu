@@ -6,11 +6,7 @@
 //                 of 64; epilogues: FP32 store / bias + GELU (pre-activation,
 //                 bf16 activation and its transpose) / bias / times
 //                 GELU'(pre-activation) (FP32, bf16 and bf16 transpose)
-//   k_mlp_fwd     fused 4-layer forward for 128 configurations per tile:
-//                 features built in shared memory, three GELU layers and the
-//                 output layer with the activations kept in shared memory and
-//                 the weights streamed through a double buffer; writes the
-//                 predicted counters, or the Eq. score of every configuration
+//   (the fused forward used for predictions and scores is k_mlp_pipe.cu)
 //   helpers       features of a training batch, transpose, loss gradient,
 //                 column sums, Adam
 //
@@ -272,183 +268,6 @@ __global__ void k_to_bf16(const float *__restrict__ p, int rows, int cols,
   }
 }
 
-// ---- fused forward -------------------------------------------------------------------------
-__device__ __forceinline__ void build_features(uint8_t *sX, const MlpDev &md, uint64_t p,
-                                               bool valid) {
-  const int F = md.F;
-  const uint4 zero = make_uint4(0, 0, 0, 0);
-  for (int c0 = 0; c0 < F; c0 += 8)
-    *reinterpret_cast<uint4 *>(sX + tc::core_off(threadIdx.x, c0, F)) = zero;
-  if (!valid) return;
-  for (int j = 0; j < md.P; ++j) {
-    const uint32_t d = nib64(p, j);
-    *reinterpret_cast<uint16_t *>(sX + tc::core_off(threadIdx.x, md.off[j] + (int)d, F)) = 0x3F80;
-    *reinterpret_cast<uint16_t *>(sX + tc::core_off(threadIdx.x, md.off[md.P] + j, F)) =
-        md.utab[j * 16 + d];
-  }
-}
-
-// MODE 0: out[i * K + c] = predicted counter c of configuration packed[i].
-// MODE 1: out[i] = Eq. score of configuration packed[i] against the profiled
-//         prediction pcprof and the expert system's delta (float32, counters
-//         ascending, the same operations as the tree path's term tables), and
-//         the minimum and maximum over entries whose `evaluated` bit is clear
-//         folded into minmax[0..1] (order-preserving integer keys).
-template <int MODE>
-__global__ void __launch_bounds__(128, 1)
-    k_mlp_fwd(const MlpDev md, const uint64_t *__restrict__ packed, int64_t n,
-              float *__restrict__ out, const float *__restrict__ pcprof,
-              const float *__restrict__ delta, const uint32_t *__restrict__ evaluated,
-              int *__restrict__ minmax, int *status) {
-  extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t *sH = sm;                          // 128 x 256 activations (KC = 256)
-  uint8_t *sW = sm + 65536;                  // 2 x (256 x 64) weight chunks
-  uint8_t *sX = sm + 131072;                 // 128 x F features (KC = F)
-  __shared__ uint64_t mbar[2];
-  __shared__ uint32_t tmem_base;
-  __shared__ float sh_pc[KTUNE_MAX_COUNTERS], sh_dl[KTUNE_MAX_COUNTERS];
-  const int warp = threadIdx.x >> 5;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
-  if (threadIdx.x == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
-  }
-  if (MODE == 1) {
-    for (int c = threadIdx.x; c < md.K; c += blockDim.x) {
-      sh_pc[c] = pcprof[c];
-      sh_dl[c] = delta[c];
-    }
-  }
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-  uint32_t ph[2] = {0u, 0u};
-  bool pend[2] = {false, false};
-  uint32_t g = 0;
-  bool ok = true;
-  float s_mn = INFINITY, s_mx = -INFINITY;
-  const int F = md.F;
-  for (int64_t t0 = blockIdx.x * (int64_t)128; t0 < n && ok; t0 += (int64_t)gridDim.x * 128) {
-    const int64_t i = t0 + threadIdx.x;
-    build_features(sX, md, i < n ? packed[i] : 0ull, i < n);
-    tc::fence_async_smem();
-    for (int l = 0; l < 4 && ok; ++l) {
-      const int Kl = l == 0 ? F : kMlpHidden;
-      const int Nl = l == 3 ? md.Kp : kMlpHidden;
-      const uint8_t *sA = l == 0 ? sX : sH;
-      for (int k0 = 0; k0 < Kl; k0 += 64, ++g) {
-        const int kc = Kl - k0 < 64 ? Kl - k0 : 64;
-        const int b = g & 1;
-        uint8_t *buf = sW + b * 32768;
-        if (pend[b]) {   // the MMAs that last read this buffer
-          ok = tc::mbar_wait(&mbar[b], ph[b], kWaitLimit) && ok;
-          ph[b] ^= 1;
-          pend[b] = false;
-        }
-        load_tile(buf, md.w[l], Kl, Nl, Nl, k0, kc);
-        tc::fence_async_smem();
-        if (!__syncthreads_and(ok)) {
-          ok = false;
-          break;
-        }
-        if (threadIdx.x == 0) {
-          tc::fence_after();
-          issue_chunk(tmem, sA, Kl, k0, buf, kc, Nl, k0 == 0);
-          tc::mma_commit(&mbar[b]);
-        }
-        pend[b] = true;
-      }
-      if (!ok) break;
-      for (int b = 0; b < 2; ++b)
-        if (pend[b]) {
-          ok = tc::mbar_wait(&mbar[b], ph[b], kWaitLimit) && ok;
-          ph[b] ^= 1;
-          pend[b] = false;
-        }
-      tc::fence_after();
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      if (l < 3) {
-        // bias + GELU, bf16, into this thread's row of sH
-        for (int c0 = 0; c0 < kMlpHidden; c0 += 16) {
-          float v[16];
-          tc::tmem_ld16(tl + c0, v);
-          uint16_t h[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) h[e] = tc::f2bf(gelu_f(__fadd_rn(v[e], md.b[l][c0 + e])));
-          *reinterpret_cast<uint4 *>(sH + tc::core_off(threadIdx.x, c0, kMlpHidden)) = pack8(h);
-          *reinterpret_cast<uint4 *>(sH + tc::core_off(threadIdx.x, c0 + 8, kMlpHidden)) =
-              pack8(h + 8);
-        }
-        tc::fence_async_smem();
-      } else if (MODE == 0) {
-        for (int c0 = 0; c0 < md.Kp; c0 += 16) {
-          float v[16];
-          tc::tmem_ld16(tl + c0, v);
-          if (i < n) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int c = c0 + e;
-              if (c < md.K)
-                out[(size_t)i * md.K + c] = __fmul_rn(__fadd_rn(v[e], md.b[3][c]), md.range[c]);
-            }
-          }
-        }
-      } else {
-        float s = 0.0f;
-        for (int c0 = 0; c0 < md.Kp; c0 += 16) {
-          float v[16];
-          tc::tmem_ld16(tl + c0, v);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int c = c0 + e;
-            if (c < md.K) {
-              const float a = __fmul_rn(__fadd_rn(v[e], md.b[3][c]), md.range[c]);
-              const float A = sh_pc[c], dl = sh_dl[c];
-              const float den = __fadd_rn(a, A);
-              float t = 0.0f;
-              if (dl != 0.0f && A != 0.0f && a != 0.0f && den != 0.0f)
-                t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(a, A), den));
-              s = __fadd_rn(s, t);
-            }
-          }
-        }
-        if (i < n) {
-          out[i] = s;
-          if (!((evaluated[i >> 5] >> (i & 31)) & 1u)) {
-            s_mn = fminf(s_mn, s);
-            s_mx = fmaxf(s_mx, s);
-          }
-        }
-      }
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-    }
-  }
-  if (!ok) {
-    for (int b = 0; b < 2; ++b)
-      if (pend[b]) tc::mbar_wait(&mbar[b], ph[b], kWaitLimit);
-    if (threadIdx.x == 0) atomicExch(status, KTUNE_ETIMEOUT);
-  } else if (MODE == 1) {
-    for (int o = 16; o; o >>= 1) {
-      s_mn = fminf(s_mn, __shfl_xor_sync(0xffffffffu, s_mn, o));
-      s_mx = fmaxf(s_mx, __shfl_xor_sync(0xffffffffu, s_mx, o));
-    }
-    if ((threadIdx.x & 31) == 0 && s_mn <= s_mx) {
-      atomicMin(minmax, okey(s_mn));
-      atomicMax(minmax + 1, okey(s_mx));
-    }
-  }
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
-}
-
 // Per-step set-up of a search scored by the MLP (one CTA): publish the step's
 // by-value parameters, Delta, reset the min / max keys, the output count and
 // the super-tile sums, and count the counters with a non-zero Delta.  Same
@@ -477,19 +296,12 @@ __global__ void __launch_bounds__(256) k_mlp_prep(const SearchDev *__restrict__ 
 }  // namespace
 
 // ---- host launchers -------------------------------------------------------------------------
-int mlp_fwd_smem(int F) { return 131072 + 256 * F; }
-
-void mlp_set_attrs(int F) {
+void mlp_set_attrs(int) {
   cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   mlp_pipe_set_attrs();
-  if (F > 0) {
-    const int smem = mlp_fwd_smem(kMlpMaxF);
-    cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  }
 }
 
 void launch_gemm_tc(int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
@@ -538,29 +350,17 @@ void launch_to_bf16(const float *p, int rows, int cols, uint16_t *wb, uint16_t *
   k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, rows, cols, wb, wt);
 }
 
+// The fused forward (k_mlp_pipe): mode 0 predicted counters, mode 1 Eq. score.
 void launch_mlp_fwd(int mode, const MlpDev &md, const uint64_t *packed, int64_t n, float *out,
                     const float *pcprof, const float *delta, const uint32_t *evaluated,
                     int *minmax, int *status, int grid, cudaStream_t st) {
-  if (md.wc && mlp_pipe_supported(md.F)) {
-    int sms = grid;
-    if (sms <= 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    launch_mlp_pipe(mode, md, packed, n, out, pcprof, delta, evaluated, minmax, status, sms, st);
-    return;
+  int sms = grid;
+  if (sms <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const int smem = mlp_fwd_smem(md.F);
-  const int64_t tiles = (n + 127) / 128;
-  if (tiles == 0) return;
-  if (grid <= 0 || grid > tiles) grid = (int)tiles;
-  if (mode == 0)
-    k_mlp_fwd<0><<<grid, 128, smem, st>>>(md, packed, n, out, pcprof, delta, evaluated, minmax,
-                                          status);
-  else
-    k_mlp_fwd<1><<<grid, 128, smem, st>>>(md, packed, n, out, pcprof, delta, evaluated, minmax,
-                                          status);
+  launch_mlp_pipe(mode, md, packed, n, out, pcprof, delta, evaluated, minmax, status, sms, st);
 }
 
 void launch_mlp_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,

@@ -14,10 +14,11 @@
 //               after the output layer, the predicted counters or the Eq.
 //               score of every configuration with the minimum and maximum
 //               over the unevaluated ones.
-// The MMAs of one tile overlap the epilogue of the other.  The arithmetic is
-// that of k_mlp_fwd (same roundings, same order within every epilogue and
-// within the score's sum over counters) except GELU, whose erf comes from a
-// published rational approximation (gelu_p) instead of erff.  Every wait is
+// The MMAs of one tile overlap the epilogue of the other.  Roundings: the
+// products accumulate in FP32 in tensor memory; bias, GELU (its erf from a
+// published rational approximation, gelu_p) and the output scale in FP32;
+// activations rounded to bfloat16; the score sums its counters in ascending
+// order, each term one float32 operation sequence.  Every wait is
 // bounded: on time-out the kernel records KTUNE_ETIMEOUT, drains its own
 // copies and MMAs (bounded) and returns.
 #include <float.h>
