@@ -1,7 +1,7 @@
 """Benchmark of the counter-guided search step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--paths all|none|mlp,batch,large,tiny]
+                    [--paths all|none|mlp,lsq,cached,batch,large,tiny]
 
 Workload of the headline line: the mid-size synthetic tuning space -- 12
 parameters, 41.3M raw / 2.26M valid configurations materialised on the
@@ -27,6 +27,10 @@ the roofline of its dominant kernel:
          counter RMSE and the tree model's on a 1% held-out sample against
          the noise-free synthetic counters; search steps scored by the fused
          tensor-core forward, and their speed against the tree path;
+  lsq    the least-squares counter model (Section 3.3.1) fitted on the
+         trees' sample: its held-out counter RMSE, and steps that predict the
+         active counters and score in one kernel, or from cached columns;
+  cached the headline search with the trees' leaf indices cached once;
   batch  64 concurrent searches (8 per space) over 8 spaces of 3.5k-988k
          valid configurations, 6-14 parameters, K in {16, 32, 40}, depth-12
          trees, one graph launch per step, kernel shape from the autotuner;
@@ -62,7 +66,7 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
-ALL_PATHS = ("mlp", "cached", "batch", "large", "tiny")
+ALL_PATHS = ("mlp", "lsq", "cached", "batch", "large", "tiny")
 # DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
 # captures summarised under profiles/ (the kernels have not changed since)
 PROFILED_TRAFFIC = {
@@ -321,6 +325,9 @@ def run_ours(args):
         if "mlp" in want:
             paths["mlp"] = path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, m, samp, traj,
                                     tree_ms=1e3 * t_total / K)
+        if "lsq" in want:
+            paths["lsq"] = path_lsq(ctx, wl, desc, roles, gpu, sp, valid, digits, m, samp, traj,
+                                    tree_ms=1e3 * t_total / K)
         if "cached" in want:
             paths["cached"] = path_cached(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "batch" in want:
@@ -480,6 +487,101 @@ def path_mlp(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp
                      "frac": ach / peak, "traffic": PROFILED_TRAFFIC["k_mlp_pipe"],
                      "peak_source": "%s bf16 burst (cuBLAS GEMM)" % ctx["src"],
                      "flop_per_config": fpc,
+                     "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
+                                      "score": kern_ms[1] / kern_ms.sum(),
+                                      "weights": kern_ms[2] / kern_ms.sum(),
+                                      "select": kern_ms[3] / kern_ms.sum()}},
+    }
+
+
+def path_lsq(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp, traj, tree_ms):
+    """The least-squares counter model (Section 3.3.1) on the headline space:
+    fitted on the trees' profile sample, counter RMSE against the trees, and
+    search steps that predict the active counters and score in one kernel
+    (fused) or from cached prediction columns."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    from paper_2102_05297_gb300 import fit
+    n = len(valid)
+    Kc = wl["K"]
+    ranges = gpu.counter_ranges()
+    Y = gpu.evaluate(digits[tree_samp])[0]
+    if wl["noise"]:
+        Y = add_noise(Y, 0, wl["noise"])
+    t0 = time.perf_counter()
+    lm = fit.fit_lsq(desc.values, digits[tree_samp], Y, roles)
+    fit_s = time.perf_counter() - t0
+    binary, regs, _ = fit.lsq_shape(desc.values)
+    mreg, T = len(regs), lm["coef"].shape[2]
+    model = kt.Model(sp, lm)
+    rest = np.setdiff1d(np.arange(n), tree_samp)
+    held = np.sort(np.random.default_rng(12).choice(rest, size=max(1, n // 100), replace=False))
+    truth = gpu.evaluate(digits[held])[0].astype(np.float64)
+    pred_all = torch.empty((n, Kc), dtype=torch.float32, device="cuda")
+    hidx = torch.from_numpy(held).cuda()
+    model.predict_device(0, n, pred_all.data_ptr(), stream)
+    torch.cuda.synchronize()
+    rm_lsq = rmse_norm(pred_all[hidx].cpu().numpy(), truth, ranges)
+    tree_model.predict_device(0, n, pred_all.data_ptr(), stream)
+    torch.cuda.synchronize()
+    rm_tree = rmse_norm(pred_all[hidx].cpu().numpy(), truth, ranges)
+    del pred_all
+
+    Wu = ctx["warmup"]
+    n_steps = min(ctx["steps"], 100)
+    hi = min(len(traj), Wu + n_steps)
+    bufs = (torch.empty(wl["k"], dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(wl["k"], dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    s = kt.Search(sp, model, k=wl["k"], seed=0, stream=stream)
+    untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
+    step_ms, _, _, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, hi, wl["k"], stream, flush)
+    s.close()
+    s = kt.Search(sp, model, k=wl["k"], seed=0, stream=stream)
+    s.set_timing(True)
+    untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
+    _, kern_ms, _, k_scored, nact = timed_device_steps(kt, torch, s, traj, Wu, hi, wl["k"], stream,
+                                                       flush)
+    s.close()
+    sc = kt.Search(sp, model, k=wl["k"], seed=0, stream=stream)
+    torch.cuda.synchronize()
+    tf = time.perf_counter()
+    sc.set_cached(True)
+    fill_ms = 1e3 * (time.perf_counter() - tf)
+    untimed_device_steps(sc, traj, 0, Wu, wl["k"], bufs, stream)
+    c_ms, _, _, c_scored, _ = timed_device_steps(kt, torch, sc, traj, Wu, hi, wl["k"], stream, flush)
+    sc.close()
+    model.close()
+    t = sum(step_ms) / 1e3
+    ns = len(step_ms)
+    # algorithmic FP32 operations per scored configuration: m(m+1)/2 products
+    # for the squares and interactions, T multiply-adds (2 operations) per
+    # active counter, and 5 for its Eq. score term (sub, add, div, mul, add)
+    flop = sum(float(k_scored) / ns * (mreg * (mreg + 1) / 2 + a * (2.0 * T + 5.0)) for a in nact)
+    ach = flop / (kern_ms[1] / 1e3)
+    mhz = float(ctx["pk"].get("sm_max_mhz", 2070.0))
+    peak = ctx["props"].multi_processor_count * 128 * 2 * mhz * 1e6
+    return {
+        "workload": "least-squares counter model on the mid_12p space: %d subspaces of the %d "
+                    "two-valued parameters, %d regressors, T = %d terms per counter, fitted on "
+                    "the trees' %.0f%% profile sample" % (1 << len(binary), len(binary), mreg, T,
+                                                          100 * wl["frac"]),
+        "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / ns,
+        "steps_per_s": ns / t, "steps": ns, "fit_s": fit_s,
+        "counter_rmse": {"lsq": rm_lsq, "tree": rm_tree,
+                         "definition": "range-normalised RMSE over all %d counters on a 1%% held-out "
+                                       "sample (%d configurations) against the noise-free synthetic "
+                                       "counters; both fitted on the same sample" % (Kc, len(held))},
+        "speedup_vs_tree": tree_ms / (1e3 * t / ns),
+        "cached": {"ms_per_step": sum(c_ms) / len(c_ms), "fill_ms": fill_ms,
+                   "value": c_scored / (sum(c_ms) / 1e3), "unit": "configs/s"},
+        "roofline": {"bound": "alu", "kernel": "k_lsq_score (prediction of the active counters + "
+                                               "Eq. score)",
+                     "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": PROFILED_TRAFFIC.get("k_lsq_score"),
+                     "peak_source": "FP32 FMA issue: SMs x 128 lanes x 2 x %.0f MHz (max SM clock)"
+                                    % mhz,
+                     "flop_per_config": "m(m+1)/2 + active counters (mean %.2f) x (2T + 5)"
+                                        % np.mean(nact),
                      "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
                                       "score": kern_ms[1] / kern_ms.sum(),
                                       "weights": kern_ms[2] / kern_ms.sum(),

@@ -159,13 +159,25 @@ const uint64_t *ktune_space_packed_device(const ktune_space *space);
 /* ---- model (Section 3.3) ----------------------------------------------------
  * Parses a model blob (little-endian):
  *   uint32 magic 0x314D544B ("KTM1"), uint32 version 1, uint32 kind (1 = tree
- *   ensemble), uint32 K (1..KTUNE_MAX_COUNTERS), int32 roles[K];
- *   kind 1: then per counter: uint32 n_nodes, int32 feature[n] (-1 = leaf),
- *   int32 threshold[n] (right iff digit > threshold), int32 left[n],
- *   int32 right[n], float value[n] (leaf values, finite); node 0 is the root.
- * Checks every index against the space (KTUNE_EMODEL), pads the trees to
- * complete trees of the ensemble's depth (<= KTUNE_MAX_DEPTH) and copies them
- * to the device.  The model keeps a pointer to the space, which must outlive it. */
+ *   ensemble, 3 = least squares), uint32 K (1..KTUNE_MAX_COUNTERS), int32 roles[K];
+ *   kind 1 (Section 3.3.2): then per counter: uint32 n_nodes, int32 feature[n]
+ *   (-1 = leaf), int32 threshold[n] (right iff digit > threshold), int32
+ *   left[n], int32 right[n], float value[n] (leaf values, finite); node 0 is
+ *   the root.  Checks every index against the space, pads the trees to
+ *   complete trees of the ensemble's depth (<= KTUNE_MAX_DEPTH).
+ *   kind 3 (Section 3.3.1): then uint32 n_sub, uint32 T, float coef[n_sub][K][T]
+ *   (finite).  The space's two-valued parameters (nb <= 12 of them) pick the
+ *   subspace, the first one the most significant bit: n_sub = 2^nb.  Its
+ *   parameters with three or more values are the m regressors, each value v
+ *   mapped to u = 2 (log2(1 + v) - lo) / (hi - lo) - 1 over the parameter's
+ *   values (all > -1, not all equal); the terms are 1, u_a (a ascending),
+ *   u_a^2, u_a u_b (a < b, lexicographic): T = 1 + 2m + m(m-1)/2.  A counter's
+ *   prediction is the float32 multiply-add chain over the terms in that
+ *   order.  Depth is reported as 0.  Searches need a materialised space and
+ *   KTUNE_SELECT_SAMPLE, and are not accepted by ktune_batch_create.
+ * Malformed blobs or a shape that does not match the space give KTUNE_EMODEL.
+ * The model is copied to the device; it keeps a pointer to the space, which
+ * must outlive it. */
 int ktune_model_load(ktune_space *space, const void *blob, size_t bytes,
                      ktune_model **out);
 int ktune_model_destroy(ktune_model *model);
@@ -240,7 +252,7 @@ int ktune_search_load(ktune_space *space, ktune_model *model, const void *buf, s
  * predicts every configuration of TS with the search's model now, into a
  * device array the search owns, one column per counter of ceil(N/8)*8
  * entries: for a tree model the leaf each configuration reaches (uint16), for
- * the MLP the predicted counter (float32); later ktune_step /
+ * the MLP and least-squares models the predicted counter (float32); later ktune_step /
  * ktune_step_device calls then compute Eq. score from the columns of the
  * counters with a non-zero Delta and c_profile prediction (trees: the step's
  * per-leaf terms indexed by the cached leaves) instead of predicting again,

@@ -24,6 +24,7 @@ Modules
            weighted draws; Philox4x32-10 counter-based generator; top-k.
   search   Algorithm 1 end to end.
   mlp      the learned surrogate (BF16 rounding points, FP32 accumulate).
+  lsq      Section 3.3.1: least-squares regression per binary-parameter subspace.
 
 Parity status of each function is stated in its docstring; the only unpinned
 part is the heuristic's selected set beyond its own definition.

@@ -611,6 +611,74 @@ int ktune_space_valid_digits(const ktune_space *s, int64_t first, int64_t count,
 const uint64_t *ktune_space_packed_device(const ktune_space *s) { return s ? s->d_packed : nullptr; }
 
 // ---------------------------------------------------------------------------
+// Kind 3, the least-squares model of Section 3.3.1: after the roles, uint32
+// n_sub, uint32 T, float coef[n_sub][K][T].  The space fixes the model's
+// shape: its two-valued parameters split 2^nb subspaces, its parameters with
+// three or more values are the m regressors (T = 1 + 2m + m(m-1)/2), each
+// regressor's value v mapped to u = 2 (log2(1 + v) - lo) / (hi - lo) - 1 over
+// its value list (float64 here, stored as float32).
+static int load_lsq(ktune_space *s, const uint8_t *b, size_t bytes, int K, const std::vector<int> &roles,
+                    ktune_model **out) {
+  LsqDev q{};
+  q.K = K;
+  const int P = s->sa.P;
+  std::vector<float> utab((size_t)P * 16, 0.0f);
+  for (int j = 0; j < P; ++j) {
+    const int r = s->sa.radix[j];
+    if (r == 2) q.bin[q.nb++] = (uint8_t)j;
+    if (r < 3) continue;
+    q.reg[q.m++] = (uint8_t)j;
+    const int64_t *v = s->values.data() + s->value_off[j];
+    double lo = INFINITY, hi = -INFINITY;
+    std::vector<double> lv(r);
+    for (int d = 0; d < r; ++d) {
+      if (v[d] <= -1) FAIL(KTUNE_EMODEL, "least-squares regressors need values > -1");
+      lv[d] = log2(1.0 + (double)v[d]);
+      lo = std::min(lo, lv[d]);
+      hi = std::max(hi, lv[d]);
+    }
+    if (!(hi > lo)) FAIL(KTUNE_EMODEL, "least-squares regressor with equal values");
+    for (int d = 0; d < r; ++d) utab[(size_t)j * 16 + d] = (float)(2.0 * (lv[d] - lo) / (hi - lo) - 1.0);
+  }
+  if (q.nb > kLsqMaxBinary) FAIL(KTUNE_EMODEL, "more than 12 two-valued parameters");
+  q.T = 1 + 2 * q.m + q.m * (q.m - 1) / 2;
+  uint32_t n_sub, T;
+  if (bytes < 8) FAIL(KTUNE_EMODEL, "blob truncated");
+  memcpy(&n_sub, b, 4);
+  memcpy(&T, b + 4, 4);
+  if (n_sub != (1u << q.nb) || T != (uint32_t)q.T)
+    FAIL(KTUNE_EMODEL, "least-squares shape does not match the space");
+  const size_t n_coef = (size_t)n_sub * K * T;
+  if (bytes != 8 + 4 * n_coef) FAIL(KTUNE_EMODEL, bytes < 8 + 4 * n_coef ? "blob truncated" : "trailing bytes in blob");
+  std::vector<float> coef(n_coef);
+  memcpy(coef.data(), b + 8, 4 * n_coef);
+  for (float c : coef)
+    if (!isfinite(c)) FAIL(KTUNE_EMODEL, "non-finite coefficient");
+  ktune_model *m = new (std::nothrow) ktune_model();
+  if (!m) FAIL(KTUNE_ENOMEM, "host allocation");
+  m->space = s;
+  m->K = K;
+  m->D = 0;
+  m->kind = 3;
+  m->roles = roles;
+  int rc;
+  if ((rc = dalloc(&m->d_lsq, 1)) || (rc = dalloc(&m->d_lsq_utab, utab.size())) ||
+      (rc = dalloc(&m->d_lsq_coef, n_coef))) {
+    ktune_model_destroy(m);
+    return rc;
+  }
+  q.utab = m->d_lsq_utab;
+  q.coef = m->d_lsq_coef;
+  if (cudaMemcpy(m->d_lsq_utab, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_lsq_coef, coef.data(), n_coef * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_lsq, &q, sizeof(q), cudaMemcpyHostToDevice) != cudaSuccess) {
+    ktune_model_destroy(m);
+    FAIL(KTUNE_ECUDA, "model upload failed");
+  }
+  *out = m;
+  return KTUNE_OK;
+}
+
 int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model **out) {
   if (!s || !blob || !out) FAIL(KTUNE_EINVAL, "null argument");
   *out = nullptr;
@@ -625,7 +693,7 @@ int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model
   uint32_t magic, ver, kind, K;
   if (!rd32(&magic) || !rd32(&ver) || !rd32(&kind) || !rd32(&K)) FAIL(KTUNE_EMODEL, "blob truncated");
   if (magic != 0x314D544Bu || ver != 1) FAIL(KTUNE_EMODEL, "bad magic or version");
-  if (kind != 1) FAIL(KTUNE_EMODEL, "unsupported model kind");
+  if (kind != 1 && kind != 3) FAIL(KTUNE_EMODEL, "unsupported model kind");
   if (K < 1 || K > KTUNE_MAX_COUNTERS) FAIL(KTUNE_EMODEL, "K out of range");
   std::vector<int> roles(K);
   for (uint32_t k = 0; k < K; ++k) {
@@ -634,6 +702,7 @@ int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model
     if ((int)r < 0 || (int)r >= KTUNE_PC_N_ROLES) FAIL(KTUNE_EMODEL, "bad counter role");
     roles[k] = (int)r;
   }
+  if (kind == 3) return load_lsq(s, b + pos, bytes - pos, (int)K, roles, out);
   struct Tree {
     std::vector<int32_t> f, t, l, r;
     std::vector<float> v;
@@ -735,6 +804,9 @@ int ktune_model_destroy(ktune_model *m) {
   }
   cudaFree(m->d_nodes);
   cudaFree(m->d_leaves);
+  cudaFree(m->d_lsq);
+  cudaFree(m->d_lsq_utab);
+  cudaFree(m->d_lsq_coef);
   delete m;
   return KTUNE_OK;
 }
@@ -753,6 +825,11 @@ int ktune_model_predict_device(const ktune_model *m, int64_t first, int64_t coun
   if (!s->d_packed) FAIL(KTUNE_ESTATE, "space is not materialised");
   if (first < 0 || count < 0 || first + count > s->n_valid) FAIL(KTUNE_EINVAL, "range out of TS");
   if (m->kind == 2) return ktune_mlp_predict_device(m->mlp, first, count, out, stream);
+  if (m->kind == 3) {
+    launch_lsq_predict(m->d_lsq, s->d_packed + first, count, out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return KTUNE_OK;
+  }
   launch_predict_full(s->d_packed + first, count, m->d_nodes, m->d_leaves, m->K, m->D, out,
                       (cudaStream_t)stream);
   CK(cudaGetLastError());
@@ -773,6 +850,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   if (s->n_valid == 0) FAIL(KTUNE_EXHAUSTED, "empty tuning space");
   if (m->kind == 2 && (!s->d_packed || o->select != KTUNE_SELECT_SAMPLE))
     FAIL(KTUNE_ESTATE, "MLP models need a materialised space and KTUNE_SELECT_SAMPLE");
+  if (m->kind == 3 && (!s->d_packed || o->select != KTUNE_SELECT_SAMPLE))
+    FAIL(KTUNE_ESTATE, "least-squares models need a materialised space and KTUNE_SELECT_SAMPLE");
   const bool otf = s->flags == KTUNE_ON_THE_FLY;
   if (otf && !s->narrow)
     FAIL(KTUNE_ESTATE, "on-the-fly spaces need all digits in one 32-bit word (sum of ceil(log2 n_values) <= 32)");
@@ -865,6 +944,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   }
   sd.nodes = m->d_nodes;
   sd.kind = m->kind;
+  sd.lsq = m->d_lsq;
   sd.leaves = m->d_leaves;
   sd.K = m->K;
   sd.D = m->D;
@@ -1001,6 +1081,10 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
                      nullptr, nullptr, nullptr, m->mlp->d_status, 1, st);
       mark(1);
       launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
+    } else if (m->kind == 3) {
+      launch_lsq_prep(h->d_srch, h->d_steps, sb, st);
+      mark(1);
+      launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
     } else {
       launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
       mark(1);
@@ -1018,6 +1102,11 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
     mark(1);
     launch_mlp_fwd(1, md, h->space->d_packed, h->space->n_valid, h->d_s, h->d_pcprof, h->d_delta,
                    h->d_eval, h->d_mm, m->mlp->d_status, h->num_sms, st);
+  } else if (m->kind == 3) {
+    // least squares: set-up with c_profile's prediction, then predict + score TS
+    launch_lsq_prep(h->d_srch, h->d_steps, sb, st);
+    mark(1);
+    launch_lsq_score(h->d_srch, h->num_sms, st);
   } else {
     launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
     mark(1);
@@ -1051,7 +1140,8 @@ static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st)
       if (t != cudaGraphNodeTypeKernel) continue;
       cudaKernelNodeParams kp{};
       CK(cudaGraphKernelNodeGetParams(nd, &kp));
-      if (kp.func == bprep_func<1>() || kp.func == mlp_prep_func()) h->prep_node = nd;
+      if (kp.func == bprep_func<1>() || kp.func == mlp_prep_func() || kp.func == lsq_prep_func())
+        h->prep_node = nd;
     }
     if (!h->prep_node) FAIL(KTUNE_ECUDA, "graph capture lost the prepare kernel");
     CK(cudaGraphInstantiate(&h->gexec, g, 0));
@@ -1519,6 +1609,7 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
     if (searches[i]->opts.select != searches[0]->opts.select)
       FAIL(KTUNE_EINVAL, "searches of a batch must share the select mode");
     if (searches[i]->model->kind == 1 && tree0 < 0) tree0 = i;
+    if (searches[i]->model->kind == 3) FAIL(KTUNE_EINVAL, "least-squares searches step on their own");
   }
   for (int i = 0; i < n; ++i)
     if (searches[i]->model->kind == 1 && searches[i]->mode != searches[tree0]->mode)

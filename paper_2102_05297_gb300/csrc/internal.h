@@ -87,6 +87,18 @@ struct alignas(4) WinDev {
   uint8_t pos[kWinBits], mask[kWinBits], dst[kWinBits];   // (W >> pos) & mask -> index bits dst..
 };
 
+// The least-squares counter model (Section 3.3.1) as its kernels read it:
+// nb binary parameters select one of 2^nb subspaces (first one most
+// significant), m regressors give the terms 1, u_a, u_a^2, u_a u_b (a < b).
+struct LsqDev {
+  int K, T, m, nb;
+  uint8_t bin[KTUNE_MAX_PARAMS];   // binary parameters, ascending
+  uint8_t reg[KTUNE_MAX_PARAMS];   // regressors (>= 3 values), ascending
+  const float *utab;               // [P][16] u per digit
+  const float *coef;               // [2^nb][K][T]
+};
+constexpr int kLsqMaxBinary = 12;  // at most 4096 subspaces
+
 // Static description of one search, uploaded once.
 struct SearchDev {
   const uint64_t *packed;     // materialised TS, nibble layout (or null)
@@ -111,7 +123,8 @@ struct SearchDev {
   uint32_t ci_stride[KTUNE_MAX_PARAMS];
   const uint8_t *nodes;
   const float *leaves;
-  int kind;                   // model kind: 1 trees, 2 MLP (scored by its own kernels)
+  int kind;                   // model kind: 1 trees, 2 MLP, 3 least squares (own kernels)
+  const LsqDev *lsq;          // kind 3: the model on the device
   uint64_t *cprof_slot;       // batched MLP search: where the prepare kernel puts c_profile
   int K, D;
   uint8_t roles[KTUNE_MAX_COUNTERS];
@@ -261,6 +274,12 @@ void launch_leaf_cols(const uint64_t *packed, int64_t N, const uint8_t *nodes, i
 void launch_cscore_leaf(const SearchDev *srch, const uint16_t *leaves, int64_t Np, int tree_bytes,
                         int terms_off, int num_sms, cudaStream_t st);
 
+// least-squares counter model (k_lsq.cu)
+void launch_lsq_predict(const LsqDev *q, const uint64_t *packed, int64_t n, float *out, cudaStream_t st);
+void launch_lsq_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb, cudaStream_t st);
+const void *lsq_prep_func();
+void launch_lsq_score(const SearchDev *srch, int num_sms, cudaStream_t st);
+
 bool mlp_pipe_supported(int F);
 void mlp_pipe_set_attrs();
 void launch_pack_wc(const uint16_t *w, int Nl, int Kl, uint8_t *dst, cudaStream_t st);
@@ -346,8 +365,10 @@ struct ktune_model {
   ktune_space *space = nullptr;
   int K = 0;
   int D = 0;
-  int kind = 1;                 // 1 trees, 2 MLP (not owned)
+  int kind = 1;                 // 1 trees, 2 MLP (not owned), 3 least squares
   ktune_mlp *mlp = nullptr;
+  ktune::LsqDev *d_lsq = nullptr;   // kind 3: descriptor, u table and coefficients
+  float *d_lsq_utab = nullptr, *d_lsq_coef = nullptr;
   std::vector<int> roles;
   uint8_t *d_nodes = nullptr;   // [K][2^D] node bytes (feature << 4 | threshold)
   float *d_leaves = nullptr;    // [K][2^D]

@@ -1,4 +1,6 @@
-"""Model creation (Section 3.3.2): one regression tree per counter.
+"""Model creation: one regression tree per counter (Section 3.3.2), or a
+least-squares polynomial per counter and binary-parameter subspace (Section
+3.3.1, ``fit_lsq``).
 
 Host-side tooling, off the search step: it turns sampled profiles (digits of
 the sampled configurations and their measured counters) into the tree
@@ -117,3 +119,42 @@ def init_mlp(F: int, K: int, hidden: int = 256, seed: int = 0) -> dict:
             "W2": w(hidden, hidden), "b2": np.zeros(hidden, np.float32),
             "W3": w(hidden, hidden), "b3": np.zeros(hidden, np.float32),
             "W4": w(K, hidden), "b4": np.zeros(K, np.float32)}
+
+
+def lsq_shape(values: List[List[int]]):
+    """Binary parameters (subspace bits, first most significant), regressors
+    (three or more values) and their u per digit: log2(1 + v) mapped linearly
+    onto [-1, 1] over the parameter's values."""
+    binary = [j for j, v in enumerate(values) if len(v) == 2]
+    regs = [j for j, v in enumerate(values) if len(v) > 2]
+    u = {}
+    for j in regs:
+        l = np.log2(np.asarray(values[j], dtype=np.float64) + 1.0)
+        u[j] = (l - l.min()) * (2.0 / (l.max() - l.min())) - 1.0
+    return binary, regs, u
+
+
+def fit_lsq(values: List[List[int]], digits: np.ndarray, Y: np.ndarray, roles: List[int]) -> dict:
+    """Least-squares model of counters Y [n][K] measured at the configurations
+    with digits [n][P]: per subspace of the binary parameters, each counter
+    regressed on 1, u_a, u_a^2 and u_a u_b (a < b) of the m regressors
+    (T = 1 + 2m + m(m-1)/2 terms, in that order), minimum-norm solution; a
+    subspace without samples takes the fit over all samples.  Coefficients
+    are returned as float32 [2^nb][K][T]."""
+    binary, regs, u = lsq_shape(values)
+    D = np.asarray(digits, dtype=np.int64)
+    Y = np.asarray(Y, dtype=np.float64).reshape(len(D), -1)
+    U = np.column_stack([u[j][D[:, j]] for j in regs]) if regs else np.zeros((len(D), 0))
+    m = U.shape[1]
+    pairs = [(a, b) for a in range(m) for b in range(a + 1, m)]
+    X = np.column_stack([np.ones(len(D))] + [U[:, a] for a in range(m)] + [U[:, a] * U[:, a] for a in range(m)]
+                        + [U[:, a] * U[:, b] for a, b in pairs])
+    sub = np.zeros(len(D), dtype=np.int64)
+    for j in binary:
+        sub = (sub << 1) | D[:, j]
+    everything = np.linalg.lstsq(X, Y, rcond=None)[0].T
+    coef = np.empty((1 << len(binary), Y.shape[1], X.shape[1]))
+    for g in range(coef.shape[0]):
+        r = np.flatnonzero(sub == g)
+        coef[g] = np.linalg.lstsq(X[r], Y[r], rcond=None)[0].T if len(r) else everything
+    return {"kind": "lsq", "roles": list(roles), "coef": coef.astype(np.float32)}

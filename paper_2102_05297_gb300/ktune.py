@@ -121,8 +121,15 @@ def _arr(a, dtype):
 
 # ---------------------------------------------------------------------------
 def model_blob(model: dict) -> bytes:
-    """Serialise a tree-ensemble model (see include/ktune.h for the layout)."""
+    """Serialise a tree ensemble ({"roles", "trees"}) or a least-squares model
+    ({"kind": "lsq", "roles", "coef" [n_sub][K][T]}); layouts in include/ktune.h."""
     roles = model["roles"]
+    if model.get("kind") == "lsq":
+        coef = np.ascontiguousarray(model["coef"], "<f4")
+        assert coef.ndim == 3 and coef.shape[1] == len(roles)
+        return b"".join([struct.pack("<4I", MODEL_MAGIC, 1, 3, len(roles)),
+                         np.asarray(roles, "<i4").tobytes(),
+                         struct.pack("<2I", coef.shape[0], coef.shape[2]), coef.tobytes()])
     out = [struct.pack("<4I", MODEL_MAGIC, 1, 1, len(roles)),
            np.asarray(roles, "<i4").tobytes()]
     for t in model["trees"]:
@@ -202,8 +209,8 @@ class Space:
 
 
 class Model:
-    """Owns a ktune_model handle: a tree ensemble (dict, see model_blob) or,
-    through ``Model.from_mlp``, a view of an Mlp."""
+    """Owns a ktune_model handle: a tree ensemble or a least-squares model
+    (dict, see model_blob) or, through ``Model.from_mlp``, a view of an Mlp."""
 
     @classmethod
     def from_mlp(cls, mlp: "Mlp") -> "Model":
