@@ -625,7 +625,10 @@ static int load_lsq(ktune_space *s, const uint8_t *b, size_t bytes, int K, const
   std::vector<float> utab((size_t)P * 16, 0.0f);
   for (int j = 0; j < P; ++j) {
     const int r = s->sa.radix[j];
-    if (r == 2) q.bin[q.nb++] = (uint8_t)j;
+    if (r == 2) {
+      q.bmask |= (uint64_t)1 << (4 * j);
+      q.bin[q.nb++] = (uint8_t)j;
+    }
     if (r < 3) continue;
     q.reg[q.m++] = (uint8_t)j;
     const int64_t *v = s->values.data() + s->value_off[j];
@@ -661,6 +664,8 @@ static int load_lsq(ktune_space *s, const uint8_t *b, size_t bytes, int K, const
   m->D = 0;
   m->kind = 3;
   m->roles = roles;
+  m->lsq_m = q.m;
+  m->lsq_nb = q.nb;
   int rc;
   if ((rc = dalloc(&m->d_lsq, 1)) || (rc = dalloc(&m->d_lsq_utab, utab.size())) ||
       (rc = dalloc(&m->d_lsq_coef, n_coef))) {
@@ -886,7 +891,9 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   }
   h->n_items = (int)items.size();
   h->grid = h->n_items;
-  const size_t tree_bytes = (size_t)pack_tree_bytes(m->D, h->mode != 1);
+  size_t tree_bytes = (size_t)pack_tree_bytes(m->D, h->mode != 1);
+  if (m->kind == 3)   // the step's coefficient pack, per counter slot
+    tree_bytes = std::max<size_t>(16, (size_t)lsq_pack_bytes(m->lsq_m, m->lsq_nb, m->K) / m->K + 16);
   int rc;
   auto fail = [&](int code) {
     ktune_search_destroy(h);
@@ -945,6 +952,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   sd.nodes = m->d_nodes;
   sd.kind = m->kind;
   sd.lsq = m->d_lsq;
+  sd.lsq_pack = m->kind == 3 && m->lsq_m <= kLsqRegM;
   sd.leaves = m->d_leaves;
   sd.K = m->K;
   sd.D = m->D;
@@ -1082,7 +1090,7 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
       mark(1);
       launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
     } else if (m->kind == 3) {
-      launch_lsq_prep(h->d_srch, h->d_steps, sb, st);
+      launch_lsq_prep(h->d_srch, h->d_steps, sb, 0, st);
       mark(1);
       launch_cscore(h->d_srch, h->d_cache, h->cache_np, h->num_sms, st);
     } else {
@@ -1104,9 +1112,9 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
                    h->d_eval, h->d_mm, m->mlp->d_status, h->num_sms, st);
   } else if (m->kind == 3) {
     // least squares: set-up with c_profile's prediction, then predict + score TS
-    launch_lsq_prep(h->d_srch, h->d_steps, sb, st);
+    launch_lsq_prep(h->d_srch, h->d_steps, sb, lsq_pack_bytes(m->lsq_m, m->lsq_nb, m->K), st);
     mark(1);
-    launch_lsq_score(h->d_srch, h->num_sms, st);
+    launch_lsq_score(h->d_srch, m->lsq_m, m->lsq_nb, m->K, h->num_sms, st);
   } else {
     launch_bprep(h->d_srch, h->d_steps, sb, 1, m->K, m->D, st);
     mark(1);
@@ -1349,6 +1357,15 @@ int ktune_search_load(ktune_space *s, ktune_model *m, const void *buf, size_t by
   return KTUNE_OK;
 }
 
+// Whether the least-squares prepare kernel writes the register kernel's pack
+// (cached steps read prediction columns instead).
+static int set_lsq_pack(ktune_search *h, bool on) {
+  if (h->model->kind != 3 || h->sdh.lsq_pack == (int)on) return KTUNE_OK;
+  h->sdh.lsq_pack = on;
+  CK(cudaMemcpy(&h->d_srch->lsq_pack, &h->sdh.lsq_pack, sizeof(int), cudaMemcpyHostToDevice));
+  return KTUNE_OK;
+}
+
 int ktune_search_set_cached(ktune_search *h, int enable) {
   if (!h) FAIL(KTUNE_EINVAL, "null search");
   if (!enable) {
@@ -1360,6 +1377,7 @@ int ktune_search_set_cached(ktune_search *h, int enable) {
       h->d_leaf_cache = nullptr;
       h->cached = false;
       drop_graph(h);
+      TRY(set_lsq_pack(h, h->model->kind == 3 && h->model->lsq_m <= kLsqRegM));
     }
     return KTUNE_OK;
   }
@@ -1410,6 +1428,7 @@ int ktune_search_set_cached(ktune_search *h, int enable) {
       FAIL(KTUNE_ETIMEOUT, "a tensor-core wait of the MLP timed out");
     }
   }
+  TRY(set_lsq_pack(h, false));
   h->cached = true;
   drop_graph(h);
   return KTUNE_OK;

@@ -92,12 +92,14 @@ struct alignas(4) WinDev {
 // significant), m regressors give the terms 1, u_a, u_a^2, u_a u_b (a < b).
 struct LsqDev {
   int K, T, m, nb;
+  uint64_t bmask;                  // bit 4j set for each binary parameter j
   uint8_t bin[KTUNE_MAX_PARAMS];   // binary parameters, ascending
   uint8_t reg[KTUNE_MAX_PARAMS];   // regressors (>= 3 values), ascending
   const float *utab;               // [P][16] u per digit
   const float *coef;               // [2^nb][K][T]
 };
 constexpr int kLsqMaxBinary = 12;  // at most 4096 subspaces
+constexpr int kLsqRegM = 10;       // regressors of the register score kernel (T <= 66)
 
 // Static description of one search, uploaded once.
 struct SearchDev {
@@ -125,6 +127,7 @@ struct SearchDev {
   const float *leaves;
   int kind;                   // model kind: 1 trees, 2 MLP, 3 least squares (own kernels)
   const LsqDev *lsq;          // kind 3: the model on the device
+  int lsq_pack;               // kind 3: the prepare kernel writes the register kernel's pack
   uint64_t *cprof_slot;       // batched MLP search: where the prepare kernel puts c_profile
   int K, D;
   uint8_t roles[KTUNE_MAX_COUNTERS];
@@ -276,9 +279,12 @@ void launch_cscore_leaf(const SearchDev *srch, const uint16_t *leaves, int64_t N
 
 // least-squares counter model (k_lsq.cu)
 void launch_lsq_predict(const LsqDev *q, const uint64_t *packed, int64_t n, float *out, cudaStream_t st);
-void launch_lsq_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb, cudaStream_t st);
+// bytes of the step's coefficient pack of the register score kernel (0 when m > kLsqRegM)
+int64_t lsq_pack_bytes(int m, int nb, int K);
+void launch_lsq_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,
+                     int64_t pack_bytes, cudaStream_t st);
 const void *lsq_prep_func();
-void launch_lsq_score(const SearchDev *srch, int num_sms, cudaStream_t st);
+void launch_lsq_score(const SearchDev *srch, int m, int nb, int K, int num_sms, cudaStream_t st);
 
 bool mlp_pipe_supported(int F);
 void mlp_pipe_set_attrs();
@@ -369,6 +375,7 @@ struct ktune_model {
   ktune_mlp *mlp = nullptr;
   ktune::LsqDev *d_lsq = nullptr;   // kind 3: descriptor, u table and coefficients
   float *d_lsq_utab = nullptr, *d_lsq_coef = nullptr;
+  int lsq_m = 0, lsq_nb = 0;        // kind 3: regressors, binary parameters
   std::vector<int> roles;
   uint8_t *d_nodes = nullptr;   // [K][2^D] node bytes (feature << 4 | threshold)
   float *d_leaves = nullptr;    // [K][2^D]

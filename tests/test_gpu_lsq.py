@@ -24,6 +24,16 @@ def kt():
     return ktune
 
 
+def load(name):
+    """A space of the workloads, or "wide_11": 11 three-valued parameters and
+    2 binary ones (m = 11 regressors, beyond the register kernel's limit of 10;
+    the general score kernel serves it)."""
+    if name == "wide_11":
+        return W.SpaceDesc("wide_11", ["p%d" % j for j in range(13)],
+                           [[1, 2, 4]] * 6 + [[0, 1]] + [[2, 8, 32]] * 5 + [[1, 3]], [])
+    return W.load_space(name)
+
+
 def random_coef(values, K, seed, scale=1.0, offset=0.0):
     d = olsq.design(values)
     rng = np.random.default_rng(seed)
@@ -47,9 +57,9 @@ def bound(values, coef, dig):
     return (d["T"] + 8) * 2.0 ** -23 * np.einsum("nkt,nt->nk", np.abs(C), np.abs(X)) + 1e-30
 
 
-@pytest.mark.parametrize("name,K", [("batch_2", 8), ("batch_3", 12), ("batch_4", 16)])
+@pytest.mark.parametrize("name,K", [("batch_2", 8), ("batch_3", 12), ("batch_4", 16), ("wide_11", 6)])
 def test_predict_matches_oracle(kt, name, K):
-    d = W.load_space(name)
+    d = load(name)
     roles = W.layout(40)[:K]
     coef = random_coef(d.values, K, seed=K)
     sp = kt.Space.from_desc(d)
@@ -90,9 +100,10 @@ def drive(s, gpu, radices, steps):
     return out
 
 
-@pytest.mark.parametrize("name,K,seed", [("batch_3", 16, 0), ("batch_4", 24, 1), ("batch_2", 12, 2)])
+@pytest.mark.parametrize("name,K,seed", [("batch_3", 16, 0), ("batch_4", 24, 1), ("batch_2", 12, 2),
+                                         ("mid_12p", 32, 3), ("wide_11", 12, 4)])
 def test_search_scores_bit_exact(kt, name, K, seed):
-    d = W.load_space(name)
+    d = load(name)
     roles = W.layout(40)[:K]
     gpu = SyntheticGPU(d, roles, seed=seed)
     coef = random_coef(d.values, K, seed=seed + 7, scale=0.2, offset=3.0)
@@ -121,9 +132,10 @@ def test_search_scores_bit_exact(kt, name, K, seed):
         s.report(gpu.evaluate(ospace.decode(d.radices, raw))[1])
 
 
-def test_cached_and_graph_steps_equal_fused(kt):
+@pytest.mark.parametrize("name", ["batch_4", "wide_11"])
+def test_cached_and_graph_steps_equal_fused(kt, name):
     import torch
-    d = W.load_space("batch_4")
+    d = load(name)
     roles = W.layout(40)[:20]
     gpu = SyntheticGPU(d, roles, seed=3)
     coef = random_coef(d.values, 20, seed=5, scale=0.3, offset=2.0)
