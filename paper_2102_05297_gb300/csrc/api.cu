@@ -952,7 +952,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   sd.nodes = m->d_nodes;
   sd.kind = m->kind;
   sd.lsq = m->d_lsq;
-  sd.lsq_pack = m->kind == 3 && m->lsq_m <= kLsqRegM;
+  sd.lsq_pack = m->kind == 3;
   sd.leaves = m->d_leaves;
   sd.K = m->K;
   sd.D = m->D;
@@ -1377,7 +1377,7 @@ int ktune_search_set_cached(ktune_search *h, int enable) {
       h->d_leaf_cache = nullptr;
       h->cached = false;
       drop_graph(h);
-      TRY(set_lsq_pack(h, h->model->kind == 3 && h->model->lsq_m <= kLsqRegM));
+      TRY(set_lsq_pack(h, h->model->kind == 3));
     }
     return KTUNE_OK;
   }

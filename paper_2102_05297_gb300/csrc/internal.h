@@ -99,7 +99,6 @@ struct LsqDev {
   const float *coef;               // [2^nb][K][T]
 };
 constexpr int kLsqMaxBinary = 12;  // at most 4096 subspaces
-constexpr int kLsqRegM = 10;       // regressors of the register score kernel (T <= 66)
 
 // Static description of one search, uploaded once.
 struct SearchDev {
@@ -127,7 +126,7 @@ struct SearchDev {
   const float *leaves;
   int kind;                   // model kind: 1 trees, 2 MLP, 3 least squares (own kernels)
   const LsqDev *lsq;          // kind 3: the model on the device
-  int lsq_pack;               // kind 3: the prepare kernel writes the register kernel's pack
+  int lsq_pack;               // kind 3: the prepare kernel writes the score kernel's pack (fused steps)
   uint64_t *cprof_slot;       // batched MLP search: where the prepare kernel puts c_profile
   int K, D;
   uint8_t roles[KTUNE_MAX_COUNTERS];
@@ -279,7 +278,7 @@ void launch_cscore_leaf(const SearchDev *srch, const uint16_t *leaves, int64_t N
 
 // least-squares counter model (k_lsq.cu)
 void launch_lsq_predict(const LsqDev *q, const uint64_t *packed, int64_t n, float *out, cudaStream_t st);
-// bytes of the step's coefficient pack of the register score kernel (0 when m > kLsqRegM)
+// bytes of a search's buffer for the step's coefficient pack (all K counters active)
 int64_t lsq_pack_bytes(int m, int nb, int K);
 void launch_lsq_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,
                      int64_t pack_bytes, cudaStream_t st);
