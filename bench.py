@@ -553,10 +553,10 @@ def path_lsq(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp
     model.close()
     t = sum(step_ms) / 1e3
     ns = len(step_ms)
-    # algorithmic FP32 operations per scored configuration: m(m+1)/2 products
-    # for the squares and interactions, T multiply-adds (2 operations) per
-    # active counter, and 5 for its Eq. score term (sub, add, div, mul, add)
-    flop = sum(float(k_scored) / ns * (mreg * (mreg + 1) / 2 + a * (2.0 * T + 5.0)) for a in nact)
+    # algorithmic FP32 operations per scored configuration: per active counter
+    # the polynomial's T - 1 multiply-adds in Horner form (2 operations each)
+    # and 5 for its Eq. score term (sub, add, div, mul, add)
+    flop = sum(float(k_scored) / ns * a * (2.0 * (T - 1) + 5.0) for a in nact)
     ach = flop / (kern_ms[1] / 1e3)
     mhz = float(ctx["pk"].get("sm_max_mhz", 2070.0))
     peak = ctx["props"].multi_processor_count * 128 * 2 * mhz * 1e6
@@ -574,13 +574,13 @@ def path_lsq(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp
         "speedup_vs_tree": tree_ms / (1e3 * t / ns),
         "cached": {"ms_per_step": sum(c_ms) / len(c_ms), "fill_ms": fill_ms,
                    "value": c_scored / (sum(c_ms) / 1e3), "unit": "configs/s"},
-        "roofline": {"bound": "alu", "kernel": "k_lsq_score (prediction of the active counters + "
-                                               "Eq. score)",
+        "roofline": {"bound": "alu", "kernel": "k_lsq_score_s (prediction of the active counters "
+                                               "+ Eq. score, subspace-sorted tiles)",
                      "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": ach / peak, "traffic": PROFILED_TRAFFIC.get("k_lsq_score"),
                      "peak_source": "FP32 FMA issue: SMs x 128 lanes x 2 x %.0f MHz (max SM clock)"
                                     % mhz,
-                     "flop_per_config": "m(m+1)/2 + active counters (mean %.2f) x (2T + 5)"
+                     "flop_per_config": "active counters (mean %.2f) x (2(T - 1) + 5)"
                                         % np.mean(nact),
                      "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
                                       "score": kern_ms[1] / kern_ms.sum(),

@@ -1,11 +1,15 @@
 """The least-squares counter model (Section 3.3.1) on the GPU against the oracle.
 
-The GPU evaluates each counter's polynomial as a float32 multiply-add chain
-over the terms (u rounded to float32), the oracle in float64: predictions
-agree within (T + 8) 2^-23 sum_t |c_t x_t|.  Eq. score and the selection are
-then checked bit for bit against the oracle's float32 score on the GPU's own
-predictions (ktune_model_predict_device runs the same chain as the fused
-step), and the cached steps against the fused ones."""
+The GPU evaluates each counter's polynomial in a float32 Horner form (u
+rounded to float32; c_0 + sum_a u_a (g_a + h_aa u_a + sum_{b>a} h_ab u_b), one
+fused multiply-add per coefficient), the oracle in float64: the Horner form's
+rounding error is at most about (2m + 3) 2^-24 sum_t |c_t x_t|, and the test
+allows (T + 8) 2^-23 sum_t |c_t x_t| (T = 1 + 2m + m(m-1)/2 >= 2m + 1).  Eq.
+score and the selection are then checked bit for bit against the oracle's
+float32 score on the GPU's own predictions (ktune_model_predict_device
+evaluates the same Horner form as the fused step), and the cached steps
+against the fused ones.  The spaces cover both fused kernels (sorted tiles
+for at most 64 subspaces, unsorted beyond) and m from 1 to 11."""
 import numpy as np
 import pytest
 
@@ -26,8 +30,7 @@ def kt():
 
 def load(name):
     """A space of the workloads, or "wide_11": 11 three-valued parameters and
-    2 binary ones (m = 11 regressors, beyond the register kernel's limit of 10;
-    the general score kernel serves it)."""
+    2 binary ones (m = 11 regressors, T = 78 terms)."""
     if name == "wide_11":
         return W.SpaceDesc("wide_11", ["p%d" % j for j in range(13)],
                            [[1, 2, 4]] * 6 + [[0, 1]] + [[2, 8, 32]] * 5 + [[1, 3]], [])
