@@ -25,6 +25,8 @@ Modules
   search   Algorithm 1 end to end.
   mlp      the learned surrogate (BF16 rounding points, FP32 accumulate).
   lsq      Section 3.3.1: least-squares regression per binary-parameter subspace.
+  nbr      steps restricted to c_profile's Hamming neighbourhood (Section 3.5
+           footnote; local search, Section 3.8.1).
 
 Parity status of each function is stated in its docstring; the only unpinned
 part is the heuristic's selected set beyond its own definition.

@@ -1,0 +1,102 @@
+"""Pins of the neighbourhood-restricted scoring oracle: the neighbourhood
+against brute force over the raw space and its size formula, the canonical
+order, and the reduction to the full step's top-k when the neighbourhood
+covers the whole space."""
+import itertools
+
+import numpy as np
+
+import workloads as W
+from workloads.synth import SyntheticGPU
+from workloads.trees import random_model
+from oracle import nbr, space as ospace
+from oracle.search import OracleSearch
+
+
+def test_size_formula():
+    for radices in ([2, 3], [6, 4, 4, 4, 2, 3], [5], [2, 2, 2, 2], [16, 1, 3]):
+        P = len(radices)
+        cp = np.zeros(P, dtype=np.int64)
+        for R in (1, 2):
+            assert len(nbr.neighbour_digits(radices, cp, R)) == nbr.count(radices, R)
+    # hand count: radices 3, 4 -> 2 + 3 at distance 1, 2 * 3 at distance 2
+    assert nbr.count([3, 4], 1) == 5 and nbr.count([3, 4], 2) == 11
+
+
+def test_against_brute_force_and_order():
+    radices = [3, 2, 4, 3]
+    rng = np.random.default_rng(0)
+    allv = np.array(list(itertools.product(*[range(r) for r in radices])))
+    for _ in range(5):
+        cp = np.array([rng.integers(r) for r in radices])
+        for R in (1, 2):
+            nd = nbr.neighbour_digits(radices, cp, R)
+            ham = (allv != cp).sum(axis=1)
+            want = {tuple(v) for v in allv[(ham >= 1) & (ham <= R)]}
+            got = [tuple(v) for v in nd]
+            assert len(got) == len(set(got)) and set(got) == want
+            dist = (nd != cp).sum(axis=1)
+            assert np.all(np.diff(dist) >= 0)             # distance 1 first
+            one = nd[dist == 1]
+            key1 = [(int(np.flatnonzero(v != cp)[0]), int(v[np.flatnonzero(v != cp)[0]])) for v in one]
+            assert key1 == sorted(key1)
+            two = nd[dist == 2]
+            key2 = []
+            for v in two:
+                i, j = np.flatnonzero(v != cp)
+                key2.append((int(i), int(j), int(v[i]), int(v[j])))
+            assert key2 == sorted(key2)
+
+
+def test_topk_equals_full_step_when_neighbourhood_covers_space():
+    # two parameters and radius 2: every other configuration is a neighbour
+    desc = W.SpaceDesc("two", ["a", "b"], [[1, 2, 4, 8, 16], [0, 1, 2, 3]], [])
+    roles = W.layout(16)
+    model = random_model(desc.radices, roles, depth=4, seed=3)
+    gpu = SyntheticGPU(desc, roles, seed=1)
+    a = nbr.NbrSearch(desc, model, radius=2, k=3, seed=5, mode="topk")
+    b = OracleSearch(desc, model, k=3, seed=5, mode="topk")
+    assert a.cprof == b.cprof
+    for _ in range(4):
+        c = gpu.evaluate(ospace.decode(desc.radices, [a.cprof_raw]))[0][0]
+        ra, sa = a.step(c)
+        rb, sb = b.step(c)
+        assert ra == rb and sa == sb
+        rt = list(gpu.evaluate(ospace.decode(desc.radices, ra))[1])
+        a.report(rt)
+        b.report(rt)
+        if a.cprof != b.cprof:
+            break
+
+
+def test_candidates_are_valid_unevaluated_neighbours():
+    desc = W.space_tiny_block_tile()
+    roles = W.layout(16)
+    model = random_model(desc.radices, roles, depth=6, seed=2)
+    gpu = SyntheticGPU(desc, roles, seed=2)
+    s = nbr.NbrSearch(desc, model, radius=2, k=5, seed=1)
+    seen = {s.cprof_raw}
+    for _ in range(6):
+        cand = s.candidates()
+        cpd = s.digits[s.cprof]
+        ham = (s.digits[cand] != cpd).sum(axis=1)
+        assert np.all((ham >= 1) & (ham <= 2)) and not s.evaluated[cand].any()
+        c = gpu.evaluate(ospace.decode(desc.radices, [s.cprof_raw]))[0][0]
+        raw, sc = s.step(c)
+        assert len(raw) == min(5, len(cand)) and len(set(raw)) == len(raw)
+        assert not (set(raw) & seen)
+        seen |= set(raw)
+        if raw:
+            s.report(list(gpu.evaluate(ospace.decode(desc.radices, raw))[1]))
+
+
+def test_empty_neighbourhood_returns_nothing():
+    desc = W.SpaceDesc("one", ["a"], [[0, 1]], [])
+    roles = W.layout(16)
+    model = random_model(desc.radices, roles, depth=2, seed=0)
+    s = nbr.NbrSearch(desc, model, radius=1, k=2, seed=0)
+    c = np.ones(16, np.float32)
+    raw, _ = s.step(c)
+    assert len(raw) == 1
+    raw2, _ = s.step(c)
+    assert raw2 == [] and s.step_no == 2
