@@ -263,6 +263,26 @@ int ktune_search_load(ktune_space *space, ktune_model *model, const void *buf, s
  * the cache.  Synchronises the search's stream. */
 int ktune_search_set_cached(ktune_search *search, int enable);
 
+/* Neighbourhood-restricted steps (the footnote of Section 3.5: score only a
+ * neighbourhood of c_profile when the space is too large to score whole; a
+ * local search on the scores, Section 3.8.1).  radius 1 or 2: later steps
+ * consider only the configurations whose digits differ from c_profile's in
+ * 1 .. radius parameters, in a canonical order (distance 1 first: parameter
+ * j ascending, then the new digit ascending; then distance 2: pairs i < j in
+ * lexicographic order, the new digit of i ascending, then that of j).  The
+ * valid unevaluated ones are scored (Eq. score), normalised over themselves
+ * and drawn with the usual integer weights and Philox draws, prefix sums in
+ * the canonical order (or the top k, ties to the lower raw index).  A step
+ * returns min(k, candidates) configurations; with no candidate it returns
+ * none and ktune_step gives KTUNE_EXHAUSTED (pick another c_profile with
+ * ktune_search_set_profile, or set radius 0).  radius 0 restores whole-space
+ * steps.  Needs a materialised space and a tree model (KTUNE_ESTATE
+ * otherwise) and at most 2^20 neighbours in the raw space (KTUNE_EINVAL).
+ * ktune_search_stats reports the candidates scored.  Not part of checkpoints;
+ * such searches are not accepted by ktune_batch_create.  Synchronises the
+ * search's stream. */
+int ktune_search_set_neighbourhood(ktune_search *search, int radius);
+
 /* Statistics of the most recent step.  kernel_ms holds the device time of
  * each kernel of that step in launch order (prepare, score, weights, select),
  * measured with CUDA events on the step's stream, only while timing is

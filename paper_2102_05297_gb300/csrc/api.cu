@@ -1030,6 +1030,8 @@ static void drop_graph(ktune_search *h) {
 
 int ktune_search_destroy(ktune_search *h) {
   if (!h) return KTUNE_OK;
+  cudaFree(h->d_nbr);
+  cudaFree(h->d_nbr_buf);
   cudaFree(h->d_cache);
   cudaFree(h->d_leaf_cache);
   void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
@@ -1080,6 +1082,15 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
     else cudaEventRecord(h->ev[i], st);
   };
   mark(0);
+  if (h->nbr_radius) {
+    // the neighbourhood of c_profile only: score, then select (its own kernels)
+    launch_nbr_step(h->d_srch, h->d_steps, sb, h->nbr_C, st);
+    mark(1);
+    mark(2);
+    mark(3);
+    mark(4);
+    return;
+  }
   if (h->cached) {
     // cached predictions: the step's set-up and c_profile prediction, then
     // Eq. score from the cached columns of the active counters
@@ -1148,7 +1159,8 @@ static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st)
       if (t != cudaGraphNodeTypeKernel) continue;
       cudaKernelNodeParams kp{};
       CK(cudaGraphKernelNodeGetParams(nd, &kp));
-      if (kp.func == bprep_func<1>() || kp.func == mlp_prep_func() || kp.func == lsq_prep_func())
+      if (kp.func == bprep_func<1>() || kp.func == mlp_prep_func() || kp.func == lsq_prep_func() ||
+          kp.func == nbr_score_func())
         h->prep_node = nd;
     }
     if (!h->prep_node) FAIL(KTUNE_ECUDA, "graph capture lost the prepare kernel");
@@ -1219,6 +1231,10 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
   h->last_raw.assign(h->h_out_raw, h->h_out_raw + n);
   h->last_packed.assign(h->h_out_packed, h->h_out_packed + n);
   h->n_evaluated += n;
+  if (h->nbr_radius) {
+    if (n == 0) FAIL(KTUNE_EXHAUSTED, "no unevaluated valid configuration in the neighbourhood");
+    return KTUNE_OK;
+  }
   if (n < k) FAIL(KTUNE_EXHAUSTED, "fewer unevaluated configurations than requested");
   return KTUNE_OK;
 }
@@ -1357,6 +1373,73 @@ int ktune_search_load(ktune_space *s, ktune_model *m, const void *buf, size_t by
   return KTUNE_OK;
 }
 
+int ktune_search_set_neighbourhood(ktune_search *h, int radius) {
+  if (!h) FAIL(KTUNE_EINVAL, "null search");
+  if (radius < 0 || radius > 2) FAIL(KTUNE_EINVAL, "neighbourhood radius must be 0, 1 or 2");
+  const ktune_space *s = h->space;
+  if (radius && (!s->d_packed || h->model->kind != 1))
+    FAIL(KTUNE_ESTATE, "neighbourhood steps need a materialised space and a tree model");
+  NbrDev nb{};
+  const int P = s->sa.P;
+  int64_t C1 = 0, C2 = 0;
+  if (radius) {
+    nb.radius = radius;
+    for (int j = 0; j < P; ++j) {
+      nb.radix_m1[j] = s->sa.radix[j] - 1;
+      nb.off1[j] = (int)C1;
+      C1 += nb.radix_m1[j];
+    }
+    nb.off1[P] = (int)C1;
+    int q = 0;
+    if (radius == 2)
+      for (int i = 0; i < P; ++i)
+        for (int j = i + 1; j < P; ++j) {
+          nb.pi[q] = (uint8_t)i;
+          nb.pj[q] = (uint8_t)j;
+          nb.off2[q] = (int)C2;
+          C2 += (int64_t)nb.radix_m1[i] * nb.radix_m1[j];
+          ++q;
+        }
+    nb.off2[q] = (int)C2;
+    nb.n_pairs = q;
+    if (C1 + C2 > kNbrMaxCandidates) FAIL(KTUNE_EINVAL, "neighbourhood larger than 2^20 configurations");
+    nb.C1 = (int)C1;
+    nb.C = (int)(C1 + C2);
+  }
+  CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : h->stream));
+  cudaFree(h->d_nbr);
+  cudaFree(h->d_nbr_buf);
+  h->d_nbr = nullptr;
+  h->d_nbr_buf = nullptr;
+  h->nbr_radius = 0;
+  h->nbr_C = 0;
+  h->sdh.nbr = nullptr;
+  if (radius) {
+    const size_t C = (size_t)std::max(1, nb.C);
+    // per candidate: ord_e 4 + s_e 4 + p_e 8; compacted: ord 4 + s 4 + p 8 + w 8; count
+    const size_t bytes = C * (4 + 4 + 8) + C * (4 + 4 + 8 + 8) + 256;
+    int rc;
+    if ((rc = dalloc(&h->d_nbr_buf, bytes)) || (rc = dalloc(&h->d_nbr, 1))) return rc;
+    uint8_t *b = h->d_nbr_buf;
+    nb.p_e = reinterpret_cast<uint64_t *>(b); b += C * 8;
+    nb.p = reinterpret_cast<uint64_t *>(b); b += C * 8;
+    nb.w = reinterpret_cast<uint64_t *>(b); b += C * 8;
+    nb.ord_e = reinterpret_cast<uint32_t *>(b); b += C * 4;
+    nb.s_e = reinterpret_cast<float *>(b); b += C * 4;
+    nb.ord = reinterpret_cast<uint32_t *>(b); b += C * 4;
+    nb.s = reinterpret_cast<float *>(b); b += C * 4;
+    nb.count = reinterpret_cast<int *>(b);
+    CK(cudaMemcpy(h->d_nbr, &nb, sizeof(nb), cudaMemcpyHostToDevice));
+    CK(cudaMemset(nb.count, 0, 4));
+    h->nbr_radius = radius;
+    h->nbr_C = nb.C;
+    h->sdh.nbr = h->d_nbr;
+  }
+  CK(cudaMemcpy(h->d_srch, &h->sdh, sizeof(SearchDev), cudaMemcpyHostToDevice));
+  drop_graph(h);
+  return KTUNE_OK;
+}
+
 // Whether the least-squares prepare kernel writes the register kernel's pack
 // (cached steps read prediction columns instead).
 static int set_lsq_pack(ktune_search *h, bool on) {
@@ -1457,6 +1540,13 @@ int ktune_search_stats(ktune_search *h, ktune_step_stats *out) {
     return f;
   };
   out->n_scored = h->last_scored;
+  if (h->nbr_radius) {
+    int nc = 0;
+    NbrDev nb;
+    CK(cudaMemcpy(&nb, h->d_nbr, sizeof(nb), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&nc, nb.count, 4, cudaMemcpyDeviceToHost));
+    out->n_scored = nc;
+  }
   out->n_active = na;
   out->depth = h->model->D;
   const bool none = mm[0] == 0x7FFFFFFF && mm[1] == (int)0x80000000;
@@ -1629,6 +1719,7 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
       FAIL(KTUNE_EINVAL, "searches of a batch must share the select mode");
     if (searches[i]->model->kind == 1 && tree0 < 0) tree0 = i;
     if (searches[i]->model->kind == 3) FAIL(KTUNE_EINVAL, "least-squares searches step on their own");
+    if (searches[i]->nbr_radius) FAIL(KTUNE_EINVAL, "neighbourhood-restricted searches step on their own");
   }
   for (int i = 0; i < n; ++i)
     if (searches[i]->model->kind == 1 && searches[i]->mode != searches[tree0]->mode)

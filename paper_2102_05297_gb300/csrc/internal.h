@@ -100,6 +100,28 @@ struct LsqDev {
 };
 constexpr int kLsqMaxBinary = 12;  // at most 4096 subspaces
 
+// Neighbourhood-restricted steps: the candidates around c_profile (Hamming
+// radius 1 or 2, canonical order) and the step's scratch.
+constexpr int kNbrMaxCandidates = 1 << 20;
+struct NbrDev {
+  int radius, C1, C, n_pairs;
+  int off1[KTUNE_MAX_PARAMS + 1];       // prefix sums of radix_j - 1 (distance 1)
+  int radix_m1[KTUNE_MAX_PARAMS];
+  uint8_t pi[KTUNE_MAX_PARAMS * (KTUNE_MAX_PARAMS - 1) / 2];   // pairs i < j, lexicographic
+  uint8_t pj[KTUNE_MAX_PARAMS * (KTUNE_MAX_PARAMS - 1) / 2];
+  int off2[KTUNE_MAX_PARAMS * (KTUNE_MAX_PARAMS - 1) / 2 + 1];  // prefix sums of (r_i-1)(r_j-1)
+  // per candidate (canonical index): TS ordinal (all ones when not scored), score, digits
+  uint32_t *ord_e;
+  float *s_e;
+  uint64_t *p_e;
+  // the scored candidates, compacted in canonical order
+  uint32_t *ord;
+  float *s;
+  uint64_t *p;
+  uint64_t *w;
+  int *count;                           // scored candidates of the last step
+};
+
 // Static description of one search, uploaded once.
 struct SearchDev {
   const uint64_t *packed;     // materialised TS, nibble layout (or null)
@@ -127,6 +149,7 @@ struct SearchDev {
   int kind;                   // model kind: 1 trees, 2 MLP, 3 least squares (own kernels)
   const LsqDev *lsq;          // kind 3: the model on the device
   int lsq_pack;               // kind 3: the prepare kernel writes the score kernel's pack (fused steps)
+  const NbrDev *nbr;          // neighbourhood-restricted steps (null: the whole space)
   uint64_t *cprof_slot;       // batched MLP search: where the prepare kernel puts c_profile
   int K, D;
   uint8_t roles[KTUNE_MAX_COUNTERS];
@@ -284,6 +307,11 @@ void launch_lsq_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<
                      int64_t pack_bytes, cudaStream_t st);
 const void *lsq_prep_func();
 void launch_lsq_score(const SearchDev *srch, int m, int nb, int K, int num_sms, cudaStream_t st);
+
+// neighbourhood-restricted steps (k_nbr.cu)
+void launch_nbr_step(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb, int C,
+                     cudaStream_t st);
+const void *nbr_score_func();
 
 bool mlp_pipe_supported(int F);
 void mlp_pipe_set_attrs();
@@ -451,6 +479,11 @@ struct ktune_search {
   uint16_t *d_leaf_cache = nullptr;
   int64_t cache_np = 0;
   bool cached = false;
+  // neighbourhood-restricted steps (radius 0: the whole space)
+  int nbr_radius = 0;
+  int nbr_C = 0;
+  ktune::NbrDev *d_nbr = nullptr;
+  uint8_t *d_nbr_buf = nullptr;        // the NbrDev arrays, one allocation
   // device buffers
   uint32_t *d_eval = nullptr;
   float *d_counters = nullptr, *d_pcprof = nullptr, *d_delta = nullptr;

@@ -71,6 +71,7 @@ _SIGS = {
     "ktune_search_stats": ([_vp, C.POINTER(ktune_step_stats)], C.c_int),
     "ktune_search_set_timing": ([_vp, C.c_int], C.c_int),
     "ktune_search_set_cached": ([_vp, C.c_int], C.c_int),
+    "ktune_search_set_neighbourhood": ([_vp, C.c_int], C.c_int),
     "ktune_search_save": ([_vp, _vp, C.POINTER(C.c_size_t)], C.c_int),
     "ktune_search_load": ([_vp, _vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)], C.c_int),
     "ktune_batch_create": ([C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)], C.c_int),
@@ -308,6 +309,11 @@ class Search:
     def set_cached(self, enable: bool = True):
         """Predict all of TS once and score later steps from the cache."""
         check(lib.ktune_search_set_cached(self.h, int(enable)), "ktune_search_set_cached")
+
+    def set_neighbourhood(self, radius: int):
+        """Restrict later steps to c_profile's Hamming neighbourhood (0: off)."""
+        check(lib.ktune_search_set_neighbourhood(self.h, int(radius)),
+              "ktune_search_set_neighbourhood")
 
     def save(self) -> bytes:
         """The search's checkpoint (ktune_search_save)."""
