@@ -1,7 +1,7 @@
 """Benchmark of the counter-guided search step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--paths all|none|mlp,lsq,cached,batch,large,tiny]
+                    [--paths all|none|mlp,lsq,cached,nbr,batch,large,tiny]
 
 Workload of the headline line: the mid-size synthetic tuning space -- 12
 parameters, 41.3M raw / 2.26M valid configurations materialised on the
@@ -31,6 +31,8 @@ the roofline of its dominant kernel:
          trees' sample: its held-out counter RMSE, and steps that predict the
          active counters and score in one kernel, or from cached columns;
   cached the headline search with the trees' leaf indices cached once;
+  nbr    the headline search with steps restricted to c_profile's Hamming-1
+         or Hamming-2 neighbourhood (latency of a step);
   batch  64 concurrent searches (8 per space) over 8 spaces of 3.5k-988k
          valid configurations, 6-14 parameters, K in {16, 32, 40}, depth-12
          trees, one graph launch per step, kernel shape from the autotuner;
@@ -66,7 +68,7 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
-ALL_PATHS = ("mlp", "lsq", "cached", "batch", "large", "tiny")
+ALL_PATHS = ("mlp", "lsq", "cached", "nbr", "batch", "large", "tiny")
 # DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
 # captures summarised under profiles/ (the kernels have not changed since)
 PROFILED_TRAFFIC = {
@@ -330,6 +332,8 @@ def run_ours(args):
                                     tree_ms=1e3 * t_total / K)
         if "cached" in want:
             paths["cached"] = path_cached(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
+        if "nbr" in want:
+            paths["nbr"] = path_nbr(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "batch" in want:
             paths["batch"] = path_batch(ctx)
         if "large" in want:
@@ -587,6 +591,32 @@ def path_lsq(ctx, wl, desc, roles, gpu, sp, valid, digits, tree_model, tree_samp
                                       "weights": kern_ms[2] / kern_ms.sum(),
                                       "select": kern_ms[3] / kern_ms.sum()}},
     }
+
+
+def path_nbr(ctx, wl, sp, m, traj, fused_ms):
+    """The headline search with neighbourhood-restricted steps: each recorded
+    c_profile's Hamming-1 and Hamming-2 neighbours only."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    Wu, n_steps = ctx["warmup"], min(ctx["steps"], 100)
+    k = wl["k"]
+    bufs = (torch.empty(k, dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(k, dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    out = {"workload": "the headline search (mid_12p, depth-12 trees, K = 32, k = 5) with each "
+                       "step restricted to the recorded c_profile's Hamming neighbourhood"}
+    hi = min(len(traj), Wu + n_steps)
+    for radius in (1, 2):
+        s = kt.Search(sp, m, k=k, seed=0, stream=stream)
+        s.set_neighbourhood(radius)
+        untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+        step_ms, _, visits, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, hi, k, stream, flush)
+        s.close()
+        ms = sum(step_ms) / len(step_ms)
+        out["radius_%d" % radius] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                                     "candidates_per_step": scored / len(step_ms),
+                                     "node_visits_per_step": visits / len(step_ms),
+                                     "speedup_vs_whole_space_step": fused_ms / ms}
+    return out
 
 
 def path_cached(ctx, wl, sp, m, traj, fused_ms):
