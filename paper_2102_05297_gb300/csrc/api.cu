@@ -1084,7 +1084,7 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
   mark(0);
   if (h->nbr_radius) {
     // the neighbourhood of c_profile only: score, then select (its own kernels)
-    launch_nbr_step(h->d_srch, h->d_steps, sb, h->nbr_C, st);
+    launch_nbr_step(h->d_srch, h->d_steps, sb, h->nbr_C, h->num_sms, st);
     mark(1);
     mark(2);
     mark(3);

@@ -310,7 +310,7 @@ void launch_lsq_score(const SearchDev *srch, int m, int nb, int K, int num_sms, 
 
 // neighbourhood-restricted steps (k_nbr.cu)
 void launch_nbr_step(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb, int C,
-                     cudaStream_t st);
+                     int num_sms, cudaStream_t st);
 const void *nbr_score_func();
 
 bool mlp_pipe_supported(int F);

@@ -8,15 +8,17 @@
 // step normalises over them and draws k with the full step's integer weights
 // and Philox draws, prefix sums in the canonical order, or takes the top k.
 //
-//   k_nbr_score   one thread per candidate: decode, constraint check, TS
-//                 ordinal (binary search over the ascending raw order),
-//                 evaluated bit, tree walks of the active counters, Eq. score;
+//   k_nbr_score   one warp per candidate: decode, constraint check, TS
+//                 ordinal (a 32-way search over the ascending raw order),
+//                 evaluated bit, one active tree per lane, Eq. score;
 //                 block 0 also does the step's set-up (c_profile's prediction,
 //                 Delta, resets)
 //   k_nbr_select  one CTA: compaction in canonical order, min / max, weights,
 //                 k draws without replacement (or top-k), outputs and marks
 #include <float.h>
 #include <limits.h>
+
+#include <algorithm>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -116,34 +118,51 @@ __global__ void __launch_bounds__(kScoreBlock) k_nbr_score(const SearchDev *__re
     sd.delta[threadIdx.x] = st.delta[threadIdx.x];
   }
   __syncthreads();
-  const int e = blockIdx.x * kScoreBlock + threadIdx.x;
-  if (e >= nb.C) return;
-  const uint64_t p = candidate(nb, cp, e);
-  uint32_t ord = 0xFFFFFFFFu;
-  float s = 0.0f;
-  if (valid_nbr(p, sd.groups, sd.sa.n_groups, sd.table)) {
-    // TS is in ascending raw order: first ordinal whose raw index is >= raw
-    const int64_t raw = raw_of(sd.sa, p);
-    int64_t lo = 0, hi = sd.N;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (raw_of(sd.sa, __ldg(sd.packed + mid)) < raw) lo = mid + 1;
-      else hi = mid;
-    }
-    if (lo < sd.N && raw_of(sd.sa, __ldg(sd.packed + lo)) == raw &&
-        !((__ldg(sd.eval + (lo >> 5)) >> (lo & 31)) & 1u)) {
-      ord = (uint32_t)lo;
-      const int na = s_na;
-      for (int a = 0; a < na; ++a) {
-        const int c = act[a];
-        const uint32_t leaf = tree_leaf(sd.nodes + (size_t)c * L, D, p);
-        s = __fadd_rn(s, term_n(__ldg(sd.leaves + (size_t)c * L + leaf), sA[a], sD[a]));
+  // one warp per candidate: every lane holds the same candidate; the TS
+  // search probes 32 positions per round, the lanes walk the active trees
+  const int lane = threadIdx.x & 31;
+  const int warps = kScoreBlock / 32;
+  const int na = s_na;
+  for (int e = blockIdx.x * warps + (threadIdx.x >> 5); e < nb.C; e += gridDim.x * warps) {
+    const uint64_t p = candidate(nb, cp, e);
+    uint32_t ord = 0xFFFFFFFFu;
+    float s = 0.0f;
+    if (valid_nbr(p, sd.groups, sd.sa.n_groups, sd.table)) {
+      // first ordinal a in [lo, hi] whose raw index is >= raw (TS ascending)
+      const int64_t raw = raw_of(sd.sa, p);
+      int64_t lo = 0, hi = sd.N;
+      while (hi - lo > 32) {
+        const int64_t m = lo + ((hi - lo) * (lane + 1)) / 33;
+        const bool below = raw_of(sd.sa, __ldg(sd.packed + m)) < raw;
+        const int c = __popc(__ballot_sync(FULL, below));
+        const int64_t m_lo = __shfl_sync(FULL, m, c > 0 ? c - 1 : 0);
+        const int64_t m_hi = __shfl_sync(FULL, m, c < 32 ? c : 31);
+        if (c > 0) lo = m_lo + 1;
+        if (c < 32) hi = m_hi;
+      }
+      const bool below = lo + lane < hi && raw_of(sd.sa, __ldg(sd.packed + lo + lane)) < raw;
+      const int64_t a = lo + __popc(__ballot_sync(FULL, below));
+      if (a < sd.N && raw_of(sd.sa, __ldg(sd.packed + a)) == raw &&
+          !((__ldg(sd.eval + (a >> 5)) >> (a & 31)) & 1u)) {
+        ord = (uint32_t)a;
+        for (int b0 = 0; b0 < na; b0 += 32) {
+          float term = 0.0f;
+          if (b0 + lane < na) {
+            const int c = act[b0 + lane];
+            const uint32_t leaf = tree_leaf(sd.nodes + (size_t)c * L, D, p);
+            term = term_n(__ldg(sd.leaves + (size_t)c * L + leaf), sA[b0 + lane], sD[b0 + lane]);
+          }
+          // the terms in ascending counter order, as every other path sums them
+          for (int b = b0; b < min(na, b0 + 32); ++b) s = __fadd_rn(s, __shfl_sync(FULL, term, b - b0));
+        }
       }
     }
+    if (lane == 0) {
+      nb.ord_e[e] = ord;
+      nb.s_e[e] = s;
+      nb.p_e[e] = p;
+    }
   }
-  nb.ord_e[e] = ord;
-  nb.s_e[e] = s;
-  nb.p_e[e] = p;
 }
 
 // Block-wide exclusive scan of one value per thread (1024 threads); returns
@@ -331,10 +350,11 @@ __global__ void __launch_bounds__(1024) k_nbr_select(const SearchDev *__restrict
 }  // namespace
 
 void launch_nbr_step(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb, int C,
-                     cudaStream_t st) {
-  const int blocks = C > 0 ? (C + kScoreBlock - 1) / kScoreBlock : 1;
+                     int num_sms, cudaStream_t st) {
+  const int warps = kScoreBlock / 32;
+  const int blocks = std::max(1, std::min((C + warps - 1) / warps, num_sms * 8));
   k_nbr_score<<<blocks, kScoreBlock, 0, st>>>(srch, steps_dev, sb);
-  k_nbr_select<<<1, 1024, 0, st>>>(srch, steps_dev);
+  k_nbr_select<<<1, C <= 4096 ? 128 : 1024, 0, st>>>(srch, steps_dev);
 }
 
 const void *nbr_score_func() { return (const void *)k_nbr_score; }
