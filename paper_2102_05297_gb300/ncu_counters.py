@@ -141,3 +141,25 @@ def counters(values: Dict[str, float], roles: Sequence[int]) -> np.ndarray:
             v = values[TABLE_METRICS[name]]
         out[k] = v
     return out
+
+
+def main(argv: Optional[Sequence[str]] = None) -> int:
+    """python -m paper_2102_05297_gb300.ncu_counters CSV ROLES [--kernel NAME]
+    prints one JSON list of counters per profiled launch (ROLES: comma-separated
+    KTUNE_PC_* role names or numbers, the model's counter layout)."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="ncu CSV -> ktune_step counters")
+    ap.add_argument("csv")
+    ap.add_argument("roles")
+    ap.add_argument("--kernel", default=None)
+    a = ap.parse_args(argv)
+    roles = [int(x) if x.isdigit() else ROLE_NAMES.index(x) for x in a.roles.split(",")]
+    with open(a.csv) as f:
+        for values in parse_csv(f.read(), a.kernel):
+            print(json.dumps([float(v) for v in counters(values, roles)]))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -69,3 +69,13 @@ def test_parse_and_convert():
     assert np.all(c[[k for k, r in enumerate(roles) if W.ROLE_NAMES[r] == "INERT"]] == 0)
     d = expert.delta_vector(roles, c, 0.7, 1000.0)    # the expert system takes them as they are
     assert np.all(np.isfinite(d)) and np.all(np.abs(d) <= 1)
+
+
+def test_command_line(tmp_path, capsys):
+    import json
+    vals = {nc.TABLE_METRICS["DRAM_RT"]: 1234.0, nc.TABLE_METRICS["WARP_E"]: 16.0}
+    lines = [HEADER] + [row(0, "k(int)", m, "", v) for m, v in vals.items()]
+    f = tmp_path / "p.csv"
+    f.write_text("\n".join(lines))
+    assert nc.main([str(f), "DRAM_RT,WARP_E,25", "--kernel", "k("]) == 0
+    assert json.loads(capsys.readouterr().out) == [1234.0, 50.0, 0.0]
