@@ -300,6 +300,22 @@ int ktune_search_stats(ktune_search *search, ktune_step_stats *out);
 /* Enable (1) or disable (0) per-kernel event timing of later steps. */
 int ktune_search_set_timing(ktune_search *search, int enable);
 
+/* Every score and integer weight of the most recent whole-space step, read
+ * back for inspection: for TS[first .. first+count), Eq. score (Section 3.5)
+ * into scores_dev (DEVICE float[count]) and w = round-half-even(s_norm 2^20)
+ * of Eq. score_normalization into weights_dev (DEVICE uint32[count]); either
+ * pointer may be NULL.  Weights exist only for KTUNE_SELECT_SAMPLE
+ * (KTUNE_ESTATE otherwise); the configurations evaluated before the step
+ * have weight 0, and so have the ones the step drew (a draw zeroes its
+ * weight, Algorithm 1).  The scores of configurations evaluated before the
+ * step are unspecified (0 for tree models on materialised spaces).
+ * Neighbourhood-restricted steps are refused (KTUNE_ESTATE).  The arrays are
+ * the search's own and are overwritten by its next step; the copies are
+ * enqueued on `stream`, so call it on the step's stream or after
+ * synchronising that stream.  KTUNE_EINVAL for a range outside TS. */
+int ktune_search_scores_device(const ktune_search *search, int64_t first, int64_t count,
+                               float *scores_dev, uint32_t *weights_dev, void *stream);
+
 /* ---- batched steps (many searches per launch) -------------------------------
  * A batch groups up to 64 searches (over any spaces and models) that share the
  * space mode (materialised one-word digits, materialised two-word digits, or
@@ -378,6 +394,19 @@ int ktune_mlp_predict(ktune_mlp *m, const int64_t *raw, int64_t n, float *out);
  * (materialised spaces); enqueued on `stream`. */
 int ktune_mlp_predict_device(ktune_mlp *m, int64_t first, int64_t count, float *out, void *stream);
 
+/* Bounded device waits of the MLP's fused forward kernel (prediction and
+ * scoring; no counterpart in the paper).  Every wait of that kernel on a
+ * copy, an MMA or another warp gives up after limit_ns nanoseconds (1e3 ..
+ * 1e10; the default is 1e9): the kernel then records KTUNE_ETIMEOUT, waits
+ * (bounded) for the copies and MMAs it already issued, releases its tensor
+ * memory and returns, and the call that launched it reports KTUNE_ETIMEOUT.
+ * stall = 1 makes later launches begin, in the copy and MMA warps before they
+ * issue anything, with a wait on a barrier that no thread arrives at, so that
+ * this wait runs out with no work in flight: a test of the time-out path that
+ * faults nothing.  stall = 0 restores normal launches.  After a time-out in a
+ * search step the search's state is unspecified (restore a checkpoint). */
+int ktune_mlp_set_wait(ktune_mlp *m, uint64_t limit_ns, int stall);
+
 /* A model handle that predicts with this MLP, for ktune_search_create: every
  * step then predicts c_profile and scores all of TS through the fused
  * tensor-core forward (a6-a8 on the MLP).  Needs a materialised space and
@@ -407,7 +436,8 @@ int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, floa
  * the caller owns and allocates nothing itself (no cudaMalloc, no cudaFree).
  *
  * It computes, for the step with measured counters `counters_dev` and profiled
- * configuration `cprof_packed`, Eq. score of every configuration of TS:
+ * configuration `cprof_packed`, the same per-configuration score that
+ * ktune_step computes, for every configuration of TS:
  *   packed_dev     device uint64[n], TS in ktune's packed form (digit j in bits
  *                  4j..4j+3), n >= 1
  *   evaluated_dev  device uint32[ceil(n/32)], bit i set = TS[i] already evaluated
@@ -417,7 +447,7 @@ int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, floa
  *   leaves_dev     device float[K][2^depth] leaf values of those trees
  *   roles          HOST int32[K] counter roles (KTUNE_PC_*)
  *   counters_dev   device float[K] measured counters of c_profile
- *   scores_dev     device float[n] out: Eq. score, 0 for evaluated entries
+ *   scores_dev     device float[n] out: the score, 0 for evaluated entries
  *   minmax_dev     device float[2] out: min and max score over unevaluated
  *                  entries (+inf / -inf when there are none)
  * The results equal those of the scoring inside ktune_step.
@@ -426,8 +456,10 @@ int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, floa
  * on every GPU that loads it until the process exits.  Sizes beyond it are
  * rejected with KTUNE_EINVAL: K * 5 * 2^depth bytes (rounded up to 16) must not
  * exceed 1 MiB - 16 KiB (K <= 40 at depth 12).  The first call on each device
- * looks up the array's device address once (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array: calls whose
+ * looks up the array's device address once (cudaGetSymbolAddress) and raises
+ * the scoring kernel's shared-memory limit there; make that first call before
+ * any stream capture.  The address stays cached for the process: after a
+ * cudaDeviceReset of a device, do not call this entry point on it again.  All calls share the array: calls whose
  * work overlaps on the GPU (other streams, other threads) race and give
  * undefined results, so serialise them.  Enqueued on `stream` (cudaStream_t),
  * without host synchronisation. */

@@ -1559,6 +1559,23 @@ int ktune_search_stats(ktune_search *h, ktune_step_stats *out) {
   return KTUNE_OK;
 }
 
+int ktune_search_scores_device(const ktune_search *h, int64_t first, int64_t count,
+                               float *scores_dev, uint32_t *weights_dev, void *stream) {
+  if (!h || (!scores_dev && !weights_dev)) FAIL(KTUNE_EINVAL, "null argument");
+  const int64_t N = h->space->n_valid;
+  if (first < 0 || count < 0 || first > N || count > N - first) FAIL(KTUNE_EINVAL, "range out of TS");
+  if (h->nbr_radius) FAIL(KTUNE_ESTATE, "neighbourhood-restricted steps score only their candidates");
+  if (weights_dev && h->opts.select != KTUNE_SELECT_SAMPLE)
+    FAIL(KTUNE_ESTATE, "top-k searches compute no weights");
+  if (count == 0) return KTUNE_OK;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (scores_dev)
+    CK(cudaMemcpyAsync(scores_dev, h->d_s + first, (size_t)count * 4, cudaMemcpyDeviceToDevice, st));
+  if (weights_dev)
+    CK(cudaMemcpyAsync(weights_dev, h->d_w + first, (size_t)count * 4, cudaMemcpyDeviceToDevice, st));
+  return KTUNE_OK;
+}
+
 int ktune_report(ktune_search *h, const double *runtimes, int n) {
   if (!h || (!runtimes && n)) FAIL(KTUNE_EINVAL, "null argument");
   if (n != (int)h->last_raw.size() || n == 0) FAIL(KTUNE_ESTATE, "no matching ktune_step to report");

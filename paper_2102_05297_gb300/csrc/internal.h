@@ -228,13 +228,16 @@ void launch_enum_write(const SpaceArgs &sa, const GroupDev *groups, const uint32
                        cudaStream_t st);
 
 // ---- search step (k_step.cu) ----
-void launch_prepare(const PrepArgs &pa, const float *counters, const uint8_t *nodes,
-                    const float *leaves, float *pcprof, float *delta32, int *n_active,
-                    int *active, uint8_t *pack, cudaStream_t st);
+// (the allocation-free scoring path: each returns the launch's own status)
+cudaError_t launch_prepare(const PrepArgs &pa, const float *counters, const uint8_t *nodes,
+                           const float *leaves, float *pcprof, float *delta32, int *n_active,
+                           int *active, uint8_t *pack, cudaStream_t st);
 int score_grid(int64_t N, int num_sms);
-void launch_score_mat(const uint64_t *packed, const uint32_t *evaluated, int64_t N,
-                      const uint8_t *pack, const int *n_active, int D, float *s,
-                      float2 *minmax, int grid, cudaStream_t st);
+// Raises k_score_mat's dynamic shared-memory limit on the current device.
+cudaError_t score_mat_device_setup();
+cudaError_t launch_score_mat(const uint64_t *packed, const uint32_t *evaluated, int64_t N,
+                             const uint8_t *pack, const int *n_active, int D, float *s,
+                             float2 *minmax, int grid, cudaStream_t st);
 void launch_narrow_pack(const uint64_t *packed, int64_t n, const PrepArgs &layout,
                         uint32_t *narrow, cudaStream_t st);
 void launch_predict_full(const uint64_t *packed, int64_t count, const uint8_t *nodes,
@@ -260,6 +263,8 @@ struct MlpDev {
   const uint16_t *utab;     // [P][16] bf16 u value per digit
   const uint8_t *wc;        // chunked operand-layout copy of w[0..3] (pipelined forward)
   uint32_t wc_off[4];       // byte offset of each layer's first chunk in wc
+  uint64_t wait_ns;         // limit of each bounded wait of the forward kernel
+  int stall;                // 1: the copy and MMA warps first wait on a barrier nothing arrives at
 };
 
 // Epilogue operands of the training GEMM (see k_gemm_tc).
@@ -534,6 +539,8 @@ struct ktune_mlp {
   int *d_off = nullptr;
   uint16_t *d_utab = nullptr;
   int adam_t = 0;
+  uint64_t wait_ns = 1000000000ull;     // bounded waits of the forward kernel (ktune_mlp_set_wait)
+  int stall = 0;
   // training set
   uint64_t *d_data = nullptr;
   float *d_target = nullptr;            // counters / range, [n][K]

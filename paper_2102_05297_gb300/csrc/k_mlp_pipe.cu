@@ -36,7 +36,7 @@ namespace ktune {
 
 namespace {
 
-constexpr uint64_t kPipeWait = 1000000000ull;             // 1 s per wait
+constexpr uint64_t kPipeWait = 1000000000ull;             // 1 s: the drain waits after a time-out
 constexpr int kActBytes = 128 * kMlpHidden * 2;           // one tile's activations (64 KB)
 constexpr int kPipeSmem = 2 * kActBytes + kMlpStages * kMlpStageBytes;
 constexpr int kEpiWarps = 16;                             // 4 per tensor-memory lane quarter
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                float *__restrict__ out, const __grid_constant__ MlpTargets tg, int *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t *ring = sm + 2 * kActBytes;
-  __shared__ uint64_t full[kMlpStages], empty[kMlpStages], acc_full[2], act_ready[2], drain;
+  __shared__ uint64_t full[kMlpStages], empty[kMlpStages], acc_full[2], act_ready[2], drain, never;
   __shared__ uint32_t tmem_base;
   __shared__ __align__(16) float sh_b[3 * kMlpHidden + 64];
   __shared__ float sh_rng[KTUNE_MAX_COUNTERS];
@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       tc::mbar_init(&act_ready[x], kEpiWarps / 2);
     }
     tc::mbar_init(&drain, 1);
+    tc::mbar_init(&never, 1);   // no thread ever arrives here (md.stall)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = threadIdx.x; i < 3 * kMlpHidden; i += blockDim.x) sh_b[i] = md.b[i >> 8][i & 255];
@@ -174,7 +175,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   if (warp == 0) {
     // ---- producer: weight chunks in job order (pair, layer, tile) -------------------
     if (lane == 0) {
-      bool ok = true;
+      // md.stall: a wait that runs out before any copy is issued
+      bool ok = !md.stall || tc::mbar_wait(&never, 0u, md.wait_ns);
       uint32_t use = 0;
       const uint32_t ring_a = tc::smem_u32(ring);
       for (int64_t p = 0; p < n_pairs && ok; ++p)
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
               const int kc = min(kMlpChunkK, Kl - k0);
               const uint32_t st = use % kMlpStages;
               if (use >= (uint32_t)kMlpStages &&
-                  !tc::mbar_wait(&empty[st], ((use / kMlpStages) - 1u) & 1u, kPipeWait)) {
+                  !tc::mbar_wait(&empty[st], ((use / kMlpStages) - 1u) & 1u, md.wait_ns)) {
                 ok = false;
                 break;
               }
@@ -204,13 +206,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   } else if (warp == 1) {
     // ---- MMA issuer ---------------------------------------------------------------
     if (lane == 0) {
-      bool ok = true;
+      // md.stall: a wait that runs out before any MMA is issued
+      bool ok = !md.stall || tc::mbar_wait(&never, 0u, md.wait_ns);
       uint32_t use = 0, aph[2] = {0u, 0u};
       const uint32_t act_a = tc::smem_u32(sm), ring_a = tc::smem_u32(ring);
       for (int64_t p = 0; p < n_pairs && ok; ++p)
         for (int l = 0; l < 4 && ok; ++l)
           for (int x = 0; x < 2 && ok; ++x) {
-            if (!tc::mbar_wait(&act_ready[x], aph[x], kPipeWait)) {
+            if (!tc::mbar_wait(&act_ready[x], aph[x], md.wait_ns)) {
               ok = false;
               break;
             }
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             for (int k0 = 0; k0 < Kl; k0 += kMlpChunkK) {
               const int kc = min(kMlpChunkK, Kl - k0);
               const uint32_t st = use % kMlpStages;
-              if (!tc::mbar_wait(&full[st], (use / kMlpStages) & 1u, kPipeWait)) {
+              if (!tc::mbar_wait(&full[st], (use / kMlpStages) & 1u, md.wait_ns)) {
                 ok = false;
                 break;
               }
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     if (n_pairs > 0) build(tile_of(0), fetch(tile_of(0)));
     for (int64_t p = 0; p < n_pairs && ok; ++p)
       for (int l = 0; l < 4; ++l) {
-        ok = __all_sync(FULL, tc::mbar_wait(&acc_full[x], aph, kPipeWait));
+        ok = __all_sync(FULL, tc::mbar_wait(&acc_full[x], aph, md.wait_ns));
         if (!ok) break;
         aph ^= 1u;
         tc::fence_after();

@@ -218,13 +218,27 @@ __global__ void k_mark(uint32_t *ev, int64_t ordinal) {
 
 }  // namespace
 
-void launch_prepare(const PrepArgs &pa, const float *counters, const uint8_t *nodes,
-                    const float *leaves, float *pcprof, float *delta32, int *n_active,
-                    int *active, uint8_t *pack, cudaStream_t st) {
+// Launch through cudaLaunchKernelEx so that the caller learns whether this
+// launch itself was accepted, independently of errors left pending by
+// unrelated earlier work on the thread.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_checked(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+cudaError_t launch_prepare(const PrepArgs &pa, const float *counters, const uint8_t *nodes,
+                           const float *leaves, float *pcprof, float *delta32, int *n_active,
+                           int *active, uint8_t *pack, cudaStream_t st) {
   const int L = 1 << pa.D;
   dim3 grid(pa.K, (L + kPrepLeaves - 1) / kPrepLeaves);
-  k_prepare<<<grid, 256, 0, st>>>(pa, counters, nodes, leaves, pcprof, delta32, n_active, active,
-                                  pack);
+  return launch_checked(k_prepare, grid, dim3(256), 0, st, pa, counters, nodes, leaves, pcprof,
+                        delta32, n_active, active, pack);
 }
 
 int score_grid(int64_t N, int num_sms) {
@@ -234,17 +248,16 @@ int score_grid(int64_t N, int num_sms) {
   return (int)(g < 1 ? 1 : g);
 }
 
-void launch_score_mat(const uint64_t *packed, const uint32_t *evaluated, int64_t N,
-                      const uint8_t *pack, const int *n_active, int D, float *s, float2 *minmax,
-                      int grid, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_score_mat<kScoreCPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSmemBudget);
-    attr = true;
-  }
-  k_score_mat<kScoreCPT><<<grid, kScoreThreads, kSmemBudget, st>>>(packed, evaluated, N, pack,
-                                                                   n_active, D, s, minmax);
+cudaError_t score_mat_device_setup() {
+  return cudaFuncSetAttribute(k_score_mat<kScoreCPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSmemBudget);
+}
+
+cudaError_t launch_score_mat(const uint64_t *packed, const uint32_t *evaluated, int64_t N,
+                             const uint8_t *pack, const int *n_active, int D, float *s,
+                             float2 *minmax, int grid, cudaStream_t st) {
+  return launch_checked(k_score_mat<kScoreCPT>, dim3(grid), dim3(kScoreThreads), kSmemBudget, st,
+                        packed, evaluated, N, pack, n_active, D, s, minmax);
 }
 
 void launch_narrow_pack(const uint64_t *packed, int64_t n, const PrepArgs &layout, uint32_t *narrow,

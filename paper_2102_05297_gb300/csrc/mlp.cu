@@ -196,6 +196,8 @@ MlpDev ktune_mlp::dev() const {
   d.utab = d_utab;
   d.wc = d_wc;
   for (int l = 0; l < 4; ++l) d.wc_off[l] = wc_off[l];
+  d.wait_ns = wait_ns;
+  d.stall = stall;
   return d;
 }
 
@@ -543,6 +545,15 @@ int ktune_mlp_predict_device(ktune_mlp *m, int64_t first, int64_t count, float *
   launch_mlp_fwd(0, m->dev(), s->d_packed + first, count, out, nullptr, nullptr, nullptr, nullptr,
                  m->d_status, sms, (cudaStream_t)stream);
   CK(cudaGetLastError());
+  return KTUNE_OK;
+}
+
+int ktune_mlp_set_wait(ktune_mlp *m, uint64_t limit_ns, int stall) {
+  if (!m) FAIL(KTUNE_EINVAL, "null argument");
+  if (limit_ns < 1000ull || limit_ns > 10000000000ull) FAIL(KTUNE_EINVAL, "limit_ns not in [1e3, 1e10]");
+  if (stall != 0 && stall != 1) FAIL(KTUNE_EINVAL, "stall must be 0 or 1");
+  m->wait_ns = limit_ns;
+  m->stall = stall;
   return KTUNE_OK;
 }
 

@@ -38,25 +38,27 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocScratchBytes]
 std::mutex g_mu;
 uint8_t *g_addr[64] = {nullptr};  // device address of the array, per device
 
-// One-time lookup, per device, of the array's device address (host code
-// cannot use the symbol itself as a pointer).
-int scratch_address(uint8_t **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    return KTUNE_ECUDA;
-  }
+// Set-up of the current device, once per device under the mutex: the array's
+// device address (host code cannot use the symbol itself as a pointer) and
+// the scoring kernel's shared-memory limit.  The address stays cached for the
+// life of the process; a cudaDeviceReset invalidates it, so a process that
+// resets a device must not call ktune_score_noalloc on it afterwards.
+int device_setup(int dev, uint8_t **out) {
   if (dev < 0 || dev >= 64) {
-    set_error("device ordinal above 63");
+    set_error("ktune_score_noalloc: device ordinal above 63");
     return KTUNE_EINVAL;
   }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
-      set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      set_error(std::string("ktune_score_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return KTUNE_ECUDA;
+    }
+    e = score_mat_device_setup();
+    if (e != cudaSuccess) {
+      set_error(std::string("ktune_score_noalloc: cudaFuncSetAttribute: ") + cudaGetErrorString(e));
       return KTUNE_ECUDA;
     }
     g_addr[dev] = static_cast<uint8_t *>(p);
@@ -125,12 +127,16 @@ extern "C" int ktune_score_noalloc(const uint64_t *packed_dev, int64_t n, const 
     }
     pa.roles[i] = (uint8_t)roles[i];
   }
-  uint8_t *base = nullptr;
-  int rc = scratch_address(&base);
-  if (rc) return rc;
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    set_error(std::string("ktune_score_noalloc: device query: ") + cudaGetErrorString(e));
+    return KTUNE_ECUDA;
+  }
+  uint8_t *base = nullptr;
+  const int rc = device_setup(dev, &base);
+  if (rc) return rc;
   int grid = score_grid(n, sms);
   if (grid > kMaxPartials) grid = kMaxPartials;
   cudaStream_t st = (cudaStream_t)stream;
@@ -140,12 +146,19 @@ extern "C" int ktune_score_noalloc(const uint64_t *packed_dev, int64_t n, const 
   float *delta = reinterpret_cast<float *>(base + kOffDelta);
   float2 *part = reinterpret_cast<float2 *>(base + kOffMinmax);
   uint8_t *pack = base + kOffPack;
-  launch_prepare(pa, counters_dev, nodes_dev, leaves_dev, pcprof, delta, n_active, active, pack, st);
-  launch_score_mat(packed_dev, evaluated_dev, n, pack, n_active, depth, scores_dev, part, grid, st);
-  k_minmax_final<<<1, 32, 0, st>>>(part, grid, minmax_dev);
-  cudaError_t e = cudaGetLastError();
+  // each launch's own status (not an error some earlier, unrelated call left pending)
+  e = launch_prepare(pa, counters_dev, nodes_dev, leaves_dev, pcprof, delta, n_active, active, pack, st);
+  if (e == cudaSuccess)
+    e = launch_score_mat(packed_dev, evaluated_dev, n, pack, n_active, depth, scores_dev, part, grid, st);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    e = cudaLaunchKernelEx(&cfg, k_minmax_final, (const float2 *)part, grid, minmax_dev);
+  }
   if (e != cudaSuccess) {
-    set_error(std::string("ktune_score_noalloc: ") + cudaGetErrorString(e));
+    set_error(std::string("ktune_score_noalloc: launch: ") + cudaGetErrorString(e));
     return KTUNE_ECUDA;
   }
   return KTUNE_OK;

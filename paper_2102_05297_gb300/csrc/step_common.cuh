@@ -125,90 +125,6 @@ __device__ __forceinline__ uint32_t narrow_word(uint32_t nb, const PrepArgs &pa)
   return (c8 << 24) | s;
 }
 
-// The same expert system run by one full warp: lane r gathers the counter of
-// role r, then lane r computes Delta of role r (the instruction lanes share
-// their fractions through shuffles for Eq. maxutil), then lane k writes the
-// float32 Delta of counter slot k.  Every formula has the operation order of
-// expert_system, so the results are bit-identical to it.
-__device__ void expert_system_warp(const float *cnt, const uint8_t *roles, int K, double r,
-                                   double cores, float *delta32, double *vals) {
-  const int lane = threadIdx.x & 31;
-  const unsigned FULL = 0xffffffffu;
-  // gather: first slot holding role `lane`
-  double v = 0.0;
-  bool has = false;
-  if (lane < KTUNE_PC_INERT) {
-    for (int k = 0; k < K; ++k)
-      if (roles[k] == lane) {
-        v = (double)cnt[k];
-        has = true;
-        break;
-      }
-    if (!has && (lane == KTUNE_PC_SM_E || lane == KTUNE_PC_WARP_E || lane == KTUNE_PC_WARP_NP_E))
-      v = 100.0;
-    vals[lane] = v;
-  }
-  const unsigned has_mask = __ballot_sync(FULL, has);
-  __syncwarp();
-  const double *V = vals;
-  double we = V[KTUNE_PC_WARP_E], wn = V[KTUNE_PC_WARP_NP_E];
-  if (we == 0.0) we = 100.0;
-  if (wn == 0.0) wn = 100.0;
-  const double ins_fitted =
-      dmul(dmul(dmul(32.0, V[KTUNE_PC_INST_EXE]), ddiv(100.0, we)), ddiv(100.0, wn));
-  const double issue_u = V[KTUNE_PC_INST_ISSUE_U];
-  const double ins_util = fmin(1.0, ddiv(issue_u, 50.0));
-  const bool is_inst = lane >= KTUNE_PC_INST_F32 && lane <= KTUNE_PC_INST_BCONV;
-  const double frac = (is_inst && ins_fitted > 0.0) ? ddiv(V[lane], ins_fitted) : 0.0;
-  // Eq. maxutil over the seven instruction classes (lanes 8..14)
-  double um = is_inst ? frac : -INFINITY;
-  for (int o = 16; o; o >>= 1) um = fmax(um, __shfl_xor_sync(FULL, um, o));
-  double D = 0.0;
-  auto mem = [&](int rt, int wt, int u, bool read) {
-    const double a = V[rt], b = V[wt], util = V[u];
-    double bb = 0.0;
-    if (dadd(a, b) > 0.0) bb = clamp01(dmul(ddiv(read ? a : b, dadd(a, b)), ddiv(util, 100.0)));
-    return -bb;
-  };
-  switch (lane) {
-    case KTUNE_PC_DRAM_RT: D = mem(KTUNE_PC_DRAM_RT, KTUNE_PC_DRAM_WT, KTUNE_PC_DRAM_U, true); break;
-    case KTUNE_PC_DRAM_WT: D = mem(KTUNE_PC_DRAM_RT, KTUNE_PC_DRAM_WT, KTUNE_PC_DRAM_U, false); break;
-    case KTUNE_PC_L2_RT: D = mem(KTUNE_PC_L2_RT, KTUNE_PC_L2_WT, KTUNE_PC_L2_U, true); break;
-    case KTUNE_PC_L2_WT: D = mem(KTUNE_PC_L2_RT, KTUNE_PC_L2_WT, KTUNE_PC_L2_U, false); break;
-    case KTUNE_PC_SHR_LT: D = mem(KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT, KTUNE_PC_SHR_U, true); break;
-    case KTUNE_PC_SHR_WT: D = mem(KTUNE_PC_SHR_LT, KTUNE_PC_SHR_WT, KTUNE_PC_SHR_U, false); break;
-    case KTUNE_PC_TEX_RWT: D = -clamp01(ddiv(V[KTUNE_PC_TEX_U], 100.0)); break;
-    case KTUNE_PC_LOC_O: {
-      const double umax = fmax(fmax(ddiv(V[KTUNE_PC_DRAM_U], 100.0), ddiv(V[KTUNE_PC_L2_U], 100.0)),
-                               ddiv(V[KTUNE_PC_TEX_U], 100.0));
-      D = -clamp01(dmul(ddiv(V[KTUNE_PC_LOC_O], 100.0), umax));
-      break;
-    }
-    case KTUNE_PC_INST_ISSUE_U:
-      D = reaction(clamp01(dmul(um, ddiv(dsub(100.0, issue_u), 100.0))), r);
-      break;
-    case KTUNE_PC_SM_E: D = clamp01(ddiv(dsub(100.0, V[KTUNE_PC_SM_E]), 100.0)); break;
-    case KTUNE_PC_GLOBAL:
-      if ((has_mask >> KTUNE_PC_GLOBAL) & 1u) {
-        const double c5 = dmul(cores, 5.0);
-        D = clamp01(fmax(0.0, ddiv(dsub(c5, V[KTUNE_PC_GLOBAL]), c5)));
-      }
-      break;
-    default:
-      if (is_inst) D = reaction(clamp01(dmul(frac, ins_util)), r);
-  }
-  __syncwarp();
-  if (lane < KTUNE_PC_INERT) vals[lane] = fmin(1.0, fmax(-1.0, D));
-  __syncwarp();
-  for (int k = lane; k < K; k += 32) {
-    const int ro = roles[k];
-    bool first = ro < KTUNE_PC_INERT;
-    for (int j = 0; j < k && first; ++j) first = roles[j] != ro;
-    delta32[k] = first ? (float)vals[ro] : 0.0f;
-  }
-  __syncwarp();
-}
-
 // ---- narrow score path (all digits in one 32-bit word) --------------------
 // One node visit: x = W << s (funnel shift by the word's low 5 bits), the
 // carry of x + word is "digit > threshold", and j = 2 j + carry moves to the

@@ -72,6 +72,7 @@ _SIGS = {
     "ktune_search_set_timing": ([_vp, C.c_int], C.c_int),
     "ktune_search_set_cached": ([_vp, C.c_int], C.c_int),
     "ktune_search_set_neighbourhood": ([_vp, C.c_int], C.c_int),
+    "ktune_search_scores_device": ([_vp, C.c_int64, C.c_int64, _vp, _vp, _vp], C.c_int),
     "ktune_search_save": ([_vp, _vp, C.POINTER(C.c_size_t)], C.c_int),
     "ktune_search_load": ([_vp, _vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)], C.c_int),
     "ktune_batch_create": ([C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)], C.c_int),
@@ -92,6 +93,7 @@ _SIGS = {
     "ktune_mlp_predict": ([_vp, _i64p, C.c_int64, _f32p], C.c_int),
     "ktune_mlp_predict_device": ([_vp, C.c_int64, C.c_int64, _vp, _vp], C.c_int),
     "ktune_model_from_mlp": ([_vp, C.POINTER(_vp)], C.c_int),
+    "ktune_mlp_set_wait": ([_vp, C.c_uint64, C.c_int], C.c_int),
     "ktune_gemm_bf16": ([_vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int,
                          _vp], C.c_int),
 }
@@ -315,6 +317,14 @@ class Search:
         check(lib.ktune_search_set_neighbourhood(self.h, int(radius)),
               "ktune_search_set_neighbourhood")
 
+    def scores_device(self, first: int, count: int, scores_ptr: int = 0, weights_ptr: int = 0,
+                      stream=None):
+        """Copy the last step's scores / integer weights of TS[first, first+count)
+        into device buffers (ktune_search_scores_device; 0 skips one)."""
+        check(lib.ktune_search_scores_device(self.h, first, count, scores_ptr or None,
+                                             weights_ptr or None, _stream_ptr(stream)),
+              "ktune_search_scores_device")
+
     def save(self) -> bytes:
         """The search's checkpoint (ktune_search_save)."""
         n = C.c_size_t(0)
@@ -490,6 +500,11 @@ class Mlp:
         check(lib.ktune_mlp_predict(self.h, raw_p, len(raw_a), out.ctypes.data_as(_f32p)),
               "ktune_mlp_predict")
         return out
+
+    def set_wait(self, limit_ns: int = 1000000000, stall: bool = False):
+        """Limit of each bounded wait of the forward kernel; stall=True makes
+        later launches wait on a barrier nothing arrives at (ktune_mlp_set_wait)."""
+        check(lib.ktune_mlp_set_wait(self.h, int(limit_ns), int(stall)), "ktune_mlp_set_wait")
 
     def predict_device(self, first: int, count: int, out_ptr: int, stream=None):
         check(lib.ktune_mlp_predict_device(self.h, first, count, out_ptr, _stream_ptr(stream)),

@@ -297,3 +297,28 @@ def test_mlp_model_rules(kt):
     s = kt.Search(sp, model, k=5)
     with pytest.raises(kt.KtuneError):
         kt.Batch([s, s])                      # the same search twice
+
+
+def test_bounded_wait_runs_out_and_the_handle_recovers(kt):
+    """Fault handling without a fault: with stall set, the forward kernel's
+    copy and MMA warps first wait on a barrier that nothing arrives at; with a
+    10 ms limit that wait runs out before any copy or MMA is issued, the
+    kernel returns and the call reports KTUNE_ETIMEOUT.  The next normal call
+    on the same handle gives the same predictions as before."""
+    import time
+    desc, roles, gpu, valid, dig, C = tiny_setup()
+    sp = kt.Space.from_desc(desc)
+    m = kt.Mlp(sp, roles, gpu.counter_ranges(), max_batch=64)
+    m.set_params(random_params(m.F, len(roles), 3))
+    ref = m.predict(valid)
+    m.set_wait(10_000_000, stall=True)
+    t0 = time.time()
+    with pytest.raises(kt.KtuneError) as e:
+        m.predict(valid)
+    assert e.value.code == kt.KTUNE_ETIMEOUT
+    assert time.time() - t0 < 10.0            # every wait gave up and the kernel returned
+    m.set_wait(1_000_000_000, stall=False)
+    np.testing.assert_array_equal(m.predict(valid), ref)
+    with pytest.raises(kt.KtuneError) as e:
+        m.set_wait(10, stall=False)           # below the allowed range
+    assert e.value.code == kt.KTUNE_EINVAL
