@@ -68,7 +68,7 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
-ALL_PATHS = ("mlp", "lsq", "cached", "nbr", "batch", "large", "tiny")
+ALL_PATHS = ("chain", "mlp", "lsq", "cached", "nbr", "batch", "large", "tiny")
 # DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
 # captures summarised under profiles/ (the kernels have not changed since)
 PROFILED_TRAFFIC = {
@@ -273,15 +273,19 @@ def run_ours(args):
             torch.empty(wl["k"], dtype=torch.float32, device="cuda").data_ptr(),
             torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
     # per-kernel times (a separate pass: events between the kernels lengthen the step)
+    fused = args.fused
     s = kt.Search(sp, m, k=wl["k"], seed=seed, stream=stream)
+    s.set_fused(fused)
     s.set_timing(True)
     untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
     _, kern_ms, visits, _, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + K, wl["k"],
                                                   stream, flush)
-    score_s = kern_ms[1] / 1e3
+    # the dominant kernel: the fused step itself, or the score kernel of the chain
+    score_s = (kern_ms[0] if fused else kern_ms[1]) / 1e3
     s.close()
     # the timed steps
     s = kt.Search(sp, m, k=wl["k"], seed=seed, stream=stream)
+    s.set_fused(fused)
     untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
     torch.cuda.synchronize()
     if dist:
@@ -298,6 +302,7 @@ def run_ours(args):
 
     # ---- end to end through the host API ---------------------------------
     s2 = kt.Search(sp, m, k=wl["k"], seed=seed, stream=stream)
+    s2.set_fused(fused)
     e2e_ms = []
     for i in range(Wu + K):
         if i >= Wu:
@@ -330,6 +335,8 @@ def run_ours(args):
         if "lsq" in want:
             paths["lsq"] = path_lsq(ctx, wl, desc, roles, gpu, sp, valid, digits, m, samp, traj,
                                     tree_ms=1e3 * t_total / K)
+        if "chain" in want and fused:
+            paths["chain"] = path_chain(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "cached" in want:
             paths["cached"] = path_cached(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "nbr" in want:
@@ -364,23 +371,10 @@ def run_ours(args):
         "data": "synthetic (seeded synthetic performance function; depth-12 trees fitted by the "
                 "library's fitter)",
         "config": describe(name, wl, desc, len(valid)),
-        "roofline": {
-            "bound": "alu",
-            "kernel": "k_bscore (tree walk + Eq. score)",
-            "achieved": achieved / 1e9,
-            "peak": peak_visits / 1e9,
-            "unit": "Gvisit/s",
-            "frac": achieved / peak_visits,
-            "traffic": PROFILED_TRAFFIC["k_bscore"],
-            "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "peak_source": "derived: %d SMs x 4 SMSPs x 32 lanes x %.0f MHz (%s sm_max) / 4 "
-                           "instructions per node visit" % (props.multi_processor_count, sm_mhz, src),
-            "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(), "score": kern_ms[1] / kern_ms.sum(),
-                             "weights": kern_ms[2] / kern_ms.sum(), "select": kern_ms[3] / kern_ms.sum()},
-        },
+        "roofline": headline_roofline(fused, kern_ms, achieved, peak_visits, props, sm_mhz, src),
         "e2e": {"value": scored_all / t_e2e, "unit": "configs/s", "h2d_bytes_per_step": bytes_h2d,
                 "d2h_bytes_per_step": bytes_d2h, "ms_per_step": 1e3 * t_e2e / K},
-        "gpu_launches": 4 * K,
+        "gpu_launches": (1 if fused else 4) * K,
         "clocks": ck,
     }
     if paths:
@@ -390,6 +384,65 @@ def run_ours(args):
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def headline_roofline(fused, kern_ms, achieved, peak_visits, props, sm_mhz, src):
+    """Roofline of the headline step's dominant kernel: the whole step as one
+    persistent kernel (its duration includes the weights and the draws), or
+    the score kernel of the four-kernel chain; algorithmic work = node visits
+    n_scored x n_active x (D + 1) per step."""
+    r = {
+        "bound": "alu",
+        "achieved": achieved / 1e9,
+        "peak": peak_visits / 1e9,
+        "unit": "Gvisit/s",
+        "frac": achieved / peak_visits,
+        "traffic_unit": "bytes per launch (ncu dram read + write)",
+        "peak_source": "derived: %d SMs x 4 SMSPs x 32 lanes x %.0f MHz (%s sm_max) / 4 "
+                       "instructions per node visit" % (props.multi_processor_count, sm_mhz, src),
+    }
+    if fused:
+        r["kernel"] = ("k_step_fused (the whole step: c_profile prediction, tree walk + Eq. score, "
+                       "weights, draws; shape %d)" % fused)
+        r["traffic"] = PROFILED_TRAFFIC.get("k_step_fused")
+    else:
+        tot = kern_ms.sum()
+        r["kernel"] = "k_bscore (tree walk + Eq. score)"
+        r["traffic"] = PROFILED_TRAFFIC["k_bscore"]
+        r["kernel_share"] = {"prepare": kern_ms[0] / tot, "score": kern_ms[1] / tot,
+                             "weights": kern_ms[2] / tot, "select": kern_ms[3] / tot}
+    return r
+
+
+def path_chain(ctx, wl, sp, m, traj, fused_ms):
+    """The headline search with four kernels per step (prepare, score,
+    weights, select; one CUDA graph): step time, per-kernel shares and the
+    score kernel's roofline, beside the fused step."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    Wu, K = ctx["warmup"], min(ctx["steps"], 300)
+    bufs = (torch.empty(wl["k"], dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(wl["k"], dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    s = kt.Search(sp, m, k=wl["k"], seed=0, stream=stream)
+    s.set_fused(0)
+    s.set_timing(True)
+    untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
+    _, kern_ms, visits, _, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + K, wl["k"], stream,
+                                                  flush)
+    s.close()
+    s = kt.Search(sp, m, k=wl["k"], seed=0, stream=stream)
+    s.set_fused(0)
+    untimed_device_steps(s, traj, 0, Wu, wl["k"], bufs, stream)
+    step_ms, _, _, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + K, wl["k"], stream,
+                                                  flush)
+    s.close()
+    t = sum(step_ms) / 1e3
+    peak_visits, sm_mhz = alu_peak(ctx["props"], ctx["pk"])
+    return {"workload": "the headline search, four kernels per step (one CUDA graph)",
+            "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / K, "steps": K,
+            "fused_speedup": (1e3 * t / K) / fused_ms,
+            "roofline": headline_roofline(0, kern_ms, visits / (kern_ms[1] / 1e3), peak_visits,
+                                          ctx["props"], sm_mhz, ctx["src"])}
 
 
 # ---------------------------------------------------------------------------
@@ -983,6 +1036,9 @@ def main():
     ap.add_argument("--mlp-train-steps", type=int, default=2000,
                     help="Adam steps (4096 rows each) of the MLP path's training")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused", type=int, default=1,
+                    help="step shape of the headline search (ktune_search_set_fused): 0 = four "
+                         "kernels, 1..3 = the whole step as one persistent kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

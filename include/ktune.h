@@ -283,11 +283,28 @@ int ktune_search_set_cached(ktune_search *search, int enable);
  * search's stream. */
 int ktune_search_set_neighbourhood(ktune_search *search, int radius);
 
+/* How whole-space steps of a tree model over a materialised space whose
+ * digits fit one 32-bit word run.  shape 0: four kernels per step (prepare,
+ * score, weights, select; on a non-default stream one CUDA graph).  shape
+ * 1..3: the whole step as ONE persistent kernel, a cooperative launch with one
+ * CTA per SM (1: 512 threads and 8 configurations per thread per chunk, 2:
+ * 1024 and 4, 3: 1024 and 8): every CTA predicts c_profile, scores a
+ * contiguous range of TS and takes part in a grid-wide barrier (its waits are
+ * bounded: a wait that gives up makes the step return KTUNE_ETIMEOUT), then
+ * its warps compute the integer weights of one sub-tile each, and the CTA that
+ * finishes last makes the draws (or merges the top-k lists).  Both give the
+ * same scores, weights and selections bit for bit.  Shape 1 is the default for
+ * the searches it applies to; other searches refuse shapes > 0 (KTUNE_ESTATE).
+ * Cached predictions and neighbourhood-restricted steps keep their own
+ * kernels.  Synchronises the search's last stream. */
+int ktune_search_set_fused(ktune_search *search, int shape);
+
 /* Statistics of the most recent step.  kernel_ms holds the device time of
- * each kernel of that step in launch order (prepare, score, weights, select),
- * measured with CUDA events on the step's stream, only while timing is
- * enabled by ktune_search_set_timing (else 0).  Synchronises the stream of
- * the last step. */
+ * each kernel of that step in launch order (prepare, score, weights, select;
+ * one entry for a fused step), measured with CUDA events on the step's
+ * stream, only while timing is enabled by ktune_search_set_timing (else 0).
+ * Synchronises the stream of the last step; returns KTUNE_ETIMEOUT (with the
+ * statistics filled in) when a barrier wait of that fused step gave up. */
 typedef struct {
   int64_t n_scored;     /* configurations scored (valid, not yet evaluated) */
   int n_active;         /* counters with a non-zero Delta and prediction for c_profile */

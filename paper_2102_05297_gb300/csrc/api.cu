@@ -1,5 +1,6 @@
 // Host side of libktune: descriptor validation, constraint tabulation, model
 // parsing and padding, search state, and the C ABI entry points (ktune.h).
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -1016,6 +1017,31 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   h->cprof_raw = raw;
   h->cprof_packed = host_pack(s, raw);
   h->n_evaluated = 1;
+  if (m->kind == 1 && h->mode == 0 && fused_blocks_per_sm(0) >= 1) {
+    // the whole step as one persistent kernel (the default where it applies)
+    const int L = 1 << m->D;
+    h->fused_grid = h->num_sms;
+    PrepArgs lay{};
+    for (int j = 0; j < s->sa.P; ++j) {
+      lay.pos[j] = s->pos[j];
+      lay.width[j] = s->width[j];
+      lay.radix[j] = (uint8_t)s->sa.radix[j];
+    }
+    const int mm0[2] = {INT_MAX, INT_MIN};
+    if ((rc = dalloc(&h->d_fz_words, (size_t)m->K * L)) || (rc = dalloc(&h->d_fz_mm, 2)) ||
+        (rc = dalloc(&h->d_fz_sync, 2)) || (rc = dalloc(&h->d_fz_status, 1)) ||
+        (rc = dalloc(&h->d_fz_cand, (size_t)h->fused_grid * KTUNE_MAX_K)))
+      return fail(rc);
+    if (launch_fused_words(m->d_nodes, m->K, m->D, lay, h->d_fz_words, cs) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_fz_mm, mm0, 8, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemsetAsync(h->d_fz_sync, 0, 16, cs) != cudaSuccess ||
+        cudaMemsetAsync(h->d_fz_status, 0, 4, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess) {
+      set_error("fused-step set-up failed");
+      return fail(KTUNE_ECUDA);
+    }
+    h->fused = 1;
+  }
   *out = h;
   return KTUNE_OK;
 }
@@ -1034,6 +1060,8 @@ int ktune_search_destroy(ktune_search *h) {
   cudaFree(h->d_nbr_buf);
   cudaFree(h->d_cache);
   cudaFree(h->d_leaf_cache);
+  void *fz[] = {h->d_fz_words, h->d_fz_mm, h->d_fz_sync, h->d_fz_status, h->d_fz_cand};
+  for (void *p : fz) cudaFree(p);
   void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
                  h->d_s, h->d_w, h->d_subsum, h->d_supsum, h->d_cand_key, h->d_cand_raw, h->d_mm, h->d_srch,
                  h->d_steps, h->d_items, h->d_sub_search, h->d_out_raw, h->d_out_score,
@@ -1179,6 +1207,18 @@ static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st)
   return KTUNE_OK;
 }
 
+// A grid-barrier wait of the fused step that gave up (read and cleared).
+static int fused_status(ktune_search *h) {
+  if (!h->last_fused) return KTUNE_OK;
+  int v = 0;
+  CK(cudaMemcpy(&v, h->d_fz_status, 4, cudaMemcpyDeviceToHost));
+  if (v) {
+    CK(cudaMemset(h->d_fz_status, 0, 4));
+    FAIL(KTUNE_ETIMEOUT, "a grid-barrier wait of the fused step timed out");
+  }
+  return KTUNE_OK;
+}
+
 static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *out_raw,
                         float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st) {
   StepBatch<1> sb{};
@@ -1192,7 +1232,23 @@ static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *
   sp.n_out = n_out;
   sp.step = h->step_no;
   sp.k = k;
-  if (st != nullptr && h->use_graph) {
+  h->last_fused = h->fused && !h->cached && !h->nbr_radius;
+  if (h->last_fused) {
+    // one cooperative launch: every CTA of the grid is resident at once
+    FusedArgs fa{};
+    fa.srch = h->d_srch;
+    fa.words = h->d_fz_words;
+    fa.mm_live = h->d_fz_mm;
+    fa.sync = h->d_fz_sync;
+    fa.status = h->d_fz_status;
+    fa.cand = h->d_fz_cand;
+    fa.wait_ns = 1000000000ull;
+    fa.st = sp;
+    if (h->timing) CK(cudaEventRecord(h->ev[0], st));
+    CK(launch_step_fused(fa, h->fused - 1, h->opts.select == KTUNE_SELECT_TOPK, h->model->D,
+                         h->fused_grid, st));
+    if (h->timing) CK(cudaEventRecord(h->ev[1], st));
+  } else if (st != nullptr && h->use_graph) {
     TRY(launch_step_graph(h, sb, st));
   } else {
     launch_step_kernels(h, sb, st, false);
@@ -1224,6 +1280,7 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
     cudaMemset(h->model->mlp->d_status, 0, 4);
     FAIL(KTUNE_ETIMEOUT, "a tensor-core wait of the MLP timed out");
   }
+  TRY(fused_status(h));
   const int n = *h->h_nout;
   *n_out = n;
   memcpy(out_raw, h->h_out_raw, n * 8);
@@ -1552,10 +1609,26 @@ int ktune_search_stats(ktune_search *h, ktune_step_stats *out) {
   const bool none = mm[0] == 0x7FFFFFFF && mm[1] == (int)0x80000000;
   out->s_min = none ? INFINITY : inv(mm[0]);
   out->s_max = none ? -INFINITY : inv(mm[1]);
-  if (h->timing) {
+  if (h->timing && h->last_fused) {
+    out->n_kernels = 1;
+    CK(cudaEventElapsedTime(&out->kernel_ms[0], h->ev[0], h->ev[1]));
+  } else if (h->timing) {
     out->n_kernels = 4;
     for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&out->kernel_ms[i], h->ev[i], h->ev[i + 1]));
   }
+  TRY(fused_status(h));
+  return KTUNE_OK;
+}
+
+int ktune_search_set_fused(ktune_search *h, int shape) {
+  if (!h) FAIL(KTUNE_EINVAL, "null search");
+  if (shape < 0 || shape > fused_shapes()) FAIL(KTUNE_EINVAL, "unknown fused-kernel shape");
+  if (shape > 0 && !h->d_fz_words)
+    FAIL(KTUNE_ESTATE, "the fused step needs a tree model on a materialised one-word space");
+  if (shape > 0 && fused_blocks_per_sm(shape - 1) < 1)
+    FAIL(KTUNE_ESTATE, "this kernel shape cannot be resident on this device");
+  CK(cudaStreamSynchronize(h->last_stream));
+  h->fused = shape;
   return KTUNE_OK;
 }
 

@@ -184,6 +184,25 @@ struct StepDev {
   float delta[KTUNE_MAX_COUNTERS];   // Delta-PC per counter slot (float32)
 };
 
+// Launch parameters of the fused whole-step kernel (k_fused.cu): a tree
+// search over a materialised one-word space, the step by value.
+struct FusedArgs {
+  const SearchDev *srch;
+  const uint32_t *words;          // [K][L] node words of the one-word walk (word 0 of a tree unused)
+  int *mm_live;                   // [2] ordered-int min / max accumulated during the step
+  unsigned long long *sync;       // [2] grid-barrier arrivals, completions (only ever grow)
+  int *status;                    // KTUNE_ETIMEOUT when a barrier wait gave up
+  uint64_t *cand;                 // [grid][KTUNE_MAX_K] per-CTA top-k keys
+  uint64_t wait_ns;               // limit of each barrier wait
+  StepDev st;
+};
+int fused_shapes();
+int fused_blocks_per_sm(int shape);
+cudaError_t launch_step_fused(const FusedArgs &fa, int shape, bool topk, int D, int grid,
+                              cudaStream_t st);
+cudaError_t launch_fused_words(const uint8_t *nodes, int K, int D, const PrepArgs &lay,
+                               uint32_t *words, cudaStream_t st);
+
 // A work item of the score kernel: a range of TS ordinals (materialised) or
 // of raw tiles (on-the-fly) of one search.
 struct ItemDev {
@@ -489,6 +508,16 @@ struct ktune_search {
   int nbr_C = 0;
   ktune::NbrDev *d_nbr = nullptr;
   uint8_t *d_nbr_buf = nullptr;        // the NbrDev arrays, one allocation
+  // the whole step as one persistent kernel (tree models, materialised
+  // one-word spaces): shape 0 = the four-kernel chain, else fused shape - 1
+  int fused = 0;
+  int fused_grid = 0;
+  bool last_fused = false;
+  uint32_t *d_fz_words = nullptr;      // [K][L] node words
+  int *d_fz_mm = nullptr;              // [2] live min / max
+  unsigned long long *d_fz_sync = nullptr;
+  int *d_fz_status = nullptr;
+  uint64_t *d_fz_cand = nullptr;       // [grid][KTUNE_MAX_K]
   // device buffers
   uint32_t *d_eval = nullptr;
   float *d_counters = nullptr, *d_pcprof = nullptr, *d_delta = nullptr;

@@ -1,0 +1,802 @@
+// One whole search step of a tree-model search over a materialised space in
+// the one-word digit layout, as a single persistent kernel (a cooperative
+// launch: one CTA per SM, all resident at once).
+//
+//   P0  every CTA: the leaf c_profile reaches in each tree (a6, Section
+//       3.3.2; warp 0, one lane per tree) and the active counters (Delta and
+//       the prediction of c_profile both non-zero, PC_used of Eq. score).
+//   P1  every CTA, a contiguous range of TS: for each group of active trees
+//       that fits shared memory, the node words are copied in and the
+//       per-leaf summands of Eq. score are computed from the leaf values;
+//       then every configuration walks the group's trees and adds the
+//       summands of the leaves it reaches (a3, a7, a8).  CTA minimum and
+//       maximum over the unevaluated ones by ordered-int atomics (a9).
+//   --  grid barrier (every wait bounded): s_min, s_max are final.
+//   P2  every warp, one 1024-configuration sub-tile at a time: Eq.
+//       score_normalization and the integer weights, the sub-tile sum and the
+//       super-tile sums (a10).
+//   P3  the CTA that finishes last: the k weighted draws without replacement
+//       of Algorithm 1 over the super-tile / sub-tile / configuration
+//       hierarchy (a11), or the merge of the CTAs' top-k lists; the picks are
+//       marked evaluated (a12).
+//
+// Every float32 operation is the one of the four-kernel step (k_bprep,
+// k_bscore, k_bweights, k_bselect), in the same order, so scores, weights and
+// selections are the same bits.
+#include <float.h>
+#include <limits.h>
+
+#include <atomic>
+
+#include "device_common.cuh"
+#include "internal.h"
+#include "step_common.cuh"
+
+namespace ktune {
+
+namespace {
+
+constexpr int kFusedSmem = 225 * 1024;   // dynamic shared memory
+
+// The kernels of this file address their dynamic shared memory through this
+// array, so that every access derived from it is known to be a shared one.
+extern __shared__ __align__(16) uint8_t fz_smem[];
+constexpr int kSpec = 16;                // draws whose sub-tile is fetched ahead
+constexpr int kF3Super = kMaxSuper;      // P3: super-tile sums in shared memory
+constexpr int kF3Sub = 4096;             // P3: sub-tile sums kept in shared memory when they fit
+static_assert(kF3Super * 8 + kF3Sub * 8 + kSpec * kSubTile * 4 <= kFusedSmem, "P3 layout");
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every CTA arrives once; returns when all G have arrived, or false after
+// limit_ns.  The counter only grows (G per barrier), so it needs no reset.
+__device__ bool grid_barrier(unsigned long long *ctr, unsigned G, uint64_t limit_ns, int *ok_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long old = atomicAdd(ctr, 1ull);
+    const unsigned long long target = (old / G + 1) * G;
+    const uint64_t t0 = gtimer();
+    int ok = 1;
+    for (;;) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (gtimer() - t0 > limit_ns) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    *ok_sh = ok;
+  }
+  __syncthreads();
+  return *ok_sh != 0;
+}
+
+// Descending list of up to k top-k keys (0 = empty) kept by one warp in
+// shared memory; a key holds the score and the ordinal (topk_key).
+__device__ __forceinline__ void key_insert(uint64_t *key, int k, uint64_t kk) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t a = lane < k ? key[lane] : 0ull;
+  const uint64_t b = lane + 32 < k ? key[lane + 32] : 0ull;
+  const int p = __popc(__ballot_sync(kFullMask, a > kk)) + __popc(__ballot_sync(kFullMask, b > kk));
+  if (p >= k) return;
+  const uint64_t pa = (lane >= 1 && lane - 1 < k) ? key[lane - 1] : 0ull;
+  const uint64_t pb = (lane + 31 < k) ? key[lane + 31] : 0ull;
+  __syncwarp();
+  if (lane < k && lane >= p) key[lane] = lane == p ? kk : pa;
+  if (lane + 32 < k && lane + 32 >= p) key[lane + 32] = lane + 32 == p ? kk : pb;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void key_offer(uint64_t *key, int k, bool ok, uint64_t kk) {
+  const uint64_t theta = key[k - 1];
+  unsigned m = __ballot_sync(kFullMask, ok && kk > theta);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    key_insert(key, k, __shfl_sync(kFullMask, kk, src));
+  }
+}
+
+// The k largest keys of n descending lists (list q at lists + q * stride),
+// by one warp: each lane holds the heads of lists lane, lane + 32, ...; every
+// round the largest head wins and its list advances.  out[r] = 0 once the
+// lists run dry.
+__device__ void warp_merge(const uint64_t *lists, int n, int stride, int k, uint64_t *out) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kPer = 8;                      // up to 256 lists
+  int head[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) head[u] = 0;
+  for (int r = 0; r < k; ++r) {
+    uint64_t best = 0;
+    int bu = -1;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = lane + 32 * u;
+      if (q < n && head[u] < k) {
+        const uint64_t v = lists[(size_t)q * stride + head[u]];
+        if (v > best) {
+          best = v;
+          bu = u;
+        }
+      }
+    }
+    uint64_t wbest = best;
+    int wl = lane;
+    for (int o = 16; o; o >>= 1) {
+      const uint64_t ob = __shfl_xor_sync(kFullMask, wbest, o);
+      const int ol = __shfl_xor_sync(kFullMask, wl, o);
+      if (ob > wbest || (ob == wbest && ol < wl)) {
+        wbest = ob;
+        wl = ol;
+      }
+    }
+    if (lane == 0) out[r] = wbest;
+    if (wbest == 0) {
+      for (int rr = r + 1; rr < k; ++rr)
+        if (lane == 0) out[rr] = 0;
+      break;
+    }
+    if (lane == wl && bu >= 0) {
+#pragma unroll
+      for (int u = 0; u < kPer; ++u)
+        if (u == bu) ++head[u];
+    }
+  }
+  __syncwarp();
+}
+
+// Walk CPT configurations (one-word digits W) through the nt staged trees and
+// add the summand of the leaf reached in each; a staged tree is 2L words:
+// node words at 1 .. L-1 (1-based heap) and the leaf summands at L .. 2L-1,
+// so the index the walk ends on addresses its summand directly.
+template <int DT, int CPT>
+__device__ __forceinline__ void walk_trees(int nt, int D, int L, const uint32_t (&W)[CPT],
+                                           float (&s)[CPT]) {
+  const uint32_t *trees = reinterpret_cast<const uint32_t *>(fz_smem);
+  for (int a = 0; a < nt; ++a) {
+    const uint32_t *t = trees + a * 2 * L;
+    uint32_t j[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) j[c] = 1u;
+    if constexpr (DT > 0) {
+#pragma unroll
+      for (int l = 0; l < DT; ++l) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], t[j[c]], W[c]);
+      }
+    } else {
+      for (int l = 0; l < D; ++l) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], t[j[c]], W[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) s[c] = __fadd_rn(s[c], __uint_as_float(t[j[c]]));
+  }
+}
+
+// P2 of the fused step: every warp of the grid, one 1024-configuration
+// sub-tile at a time: Eq. score_normalization over the unevaluated
+// configurations, integer weights, the sub-tile sum and the super-tile sums.
+// Out of line, so that its registers do not count against the walk's.
+__device__ __noinline__ void fused_weights(const FusedArgs &fa) {
+  const SearchDev &sd = *fa.srch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const unsigned G = gridDim.x;
+  const int64_t N = sd.N;
+  const float smin = okey_inv(__ldcg(fa.mm_live)), smax = okey_inv(__ldcg(fa.mm_live + 1));
+  const float gm = sd.gamma;
+  const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
+  for (int64_t gsub = (int64_t)blockIdx.x * NW + warp; gsub < n_sub; gsub += (int64_t)G * NW) {
+    const int64_t i0 = gsub * kSubTile;
+    const int64_t ew = (i0 >> 5) + lane;                          // the sub-tile's 32 words
+    const uint32_t evw = ew < ((N + 31) >> 5) ? __ldcg(sd.eval + ew) : 0u;
+    uint64_t acc = 0;
+#pragma unroll
+    for (int q = 0; q < kSubTile / 128; ++q) {
+      const int64_t i = i0 + q * 128 + lane * 4;
+      const uint32_t e = __shfl_sync(kFullMask, evw, q * 4 + (lane >> 3)) >> ((lane & 7) * 4);
+      if (i + 3 < N) {
+        const float4 s4 = __ldcg(reinterpret_cast<const float4 *>(sd.s + i));
+        const float sa[4] = {s4.x, s4.y, s4.z, s4.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          w[c] = ((e >> c) & 1u) ? 0u : (uint32_t)weight_of(sa[c], smin, smax, gm);
+          acc += w[c];
+        }
+        __stcg(reinterpret_cast<uint4 *>(sd.w + i), make_uint4(w[0], w[1], w[2], w[3]));
+      } else {
+        for (int c = 0; c < 4; ++c) {
+          if (i + c < N) {
+            const uint32_t w = ((e >> c) & 1u) ? 0u : (uint32_t)weight_of(__ldcg(sd.s + i + c), smin, smax, gm);
+            __stcg(sd.w + i + c, w);
+            acc += w;
+          }
+        }
+      }
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
+    if (lane == 0) {
+      sd.sub_sum[gsub] = acc;
+      if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(sd.super_sum + gsub / kSuper),
+                         (unsigned long long)acc);
+    }
+  }
+}
+
+// P3 of the fused step in sample mode, by the CTA that finishes last: the k
+// draws without replacement of Algorithm 1; returns how many were made (fewer
+// than k once every remaining weight is 0) with their ordinals in pick[].
+// Out of line, so that its registers do not count against the walk's.
+__device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
+  const SearchDev &sd = *fa.srch;
+  const StepDev &st = fa.st;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int THREADS = blockDim.x;
+  const int64_t N = sd.N;
+  const int k = st.k;
+  uint8_t *smem = fz_smem;
+  __shared__ int sh_n;
+  // k draws without replacement: super-tile -> sub-tile -> configuration,
+  // each a warp scan.  The sub-tiles of the first kSpec draws, as they
+  // would fall without the earlier draws' removals, are fetched in parallel
+  // first; a draw that lands in a fetched sub-tile reads its weights from
+  // shared memory (a draw zeroes its weight there too).
+  const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
+  const int64_t n_super = (n_sub + kSuper - 1) / kSuper;
+  uint64_t *sup = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *subc = sup + kF3Super;
+  uint32_t *buf = reinterpret_cast<uint32_t *>(subc + kF3Sub);
+  __shared__ int64_t spec_g[kSpec];
+  const bool cached = n_sub <= kF3Sub;
+  for (int64_t i = threadIdx.x; i < n_super; i += THREADS) sup[i] = __ldcg(sd.super_sum + i);
+  if (cached)
+    for (int64_t i = threadIdx.x; i < n_sub; i += THREADS) subc[i] = __ldcg(sd.sub_sum + i);
+  if (threadIdx.x < kSpec) spec_g[threadIdx.x] = -1;
+  __syncthreads();
+  const uint64_t seed = sd.seed;
+  const uint32_t sid = sd.search_id, stp = st.step;
+  const int64_t per = (n_super + 31) / 32;
+  const int64_t slo = min(n_super, per * lane), shi = min(n_super, slo + per);
+  // locate draw value r: super-tile sp, sub-tile g and the remainder r2
+  // within it (called by a whole warp; false if the sums are inconsistent)
+  auto locate = [&](uint64_t r, uint64_t local, uint64_t incl, int64_t &sp_o, int64_t &g_o,
+                    uint64_t &vg_o, uint64_t &r2_o) -> bool {
+    int64_t sp_sel = -1;
+    uint64_t r1 = 0;
+    if (incl - local <= r && r < incl) {
+      uint64_t acc = incl - local;
+      for (int64_t sp = slo; sp < shi; ++sp) {
+        if (r < acc + sup[sp]) {
+          sp_sel = sp;
+          r1 = r - acc;
+          break;
+        }
+        acc += sup[sp];
+      }
+    }
+    const int src1 = __ffs(__ballot_sync(kFullMask, sp_sel >= 0)) - 1;
+    if (src1 < 0) return false;
+    sp_sel = __shfl_sync(kFullMask, sp_sel, src1);
+    r1 = __shfl_sync(kFullMask, r1, src1);
+    const int64_t gl = sp_sel * kSuper + lane;
+    const uint64_t v = gl < n_sub ? (cached ? subc[gl] : __ldcg(sd.sub_sum + gl)) : 0ull;
+    const uint64_t inc = warp_incl(v);
+    const int src2 = __ffs(__ballot_sync(kFullMask, inc - v <= r1 && r1 < inc)) - 1;
+    if (src2 < 0) return false;
+    g_o = __shfl_sync(kFullMask, gl, src2);
+    vg_o = __shfl_sync(kFullMask, v, src2);
+    r2_o = r1 - __shfl_sync(kFullMask, inc - v, src2);
+    sp_o = sp_sel;
+    return g_o >= 0 && g_o < n_sub;
+  };
+  auto totals = [&](uint64_t &local, uint64_t &incl) -> uint64_t {
+    local = 0;
+    for (int64_t sp = slo; sp < shi; ++sp) local += sup[sp];
+    incl = warp_incl(local);
+    return __shfl_sync(kFullMask, incl, 31);
+  };
+  // speculative fetch: warp w takes draw w
+  if (warp < min(k, kSpec)) {
+    uint64_t local, incl;
+    const uint64_t W = totals(local, incl);
+    if (W > 0) {
+      const uint64_t r = scaled_draw(philox_u64(seed, sid, stp, (uint32_t)warp, 0u), W);
+      int64_t sp, g;
+      uint64_t vg, r2;
+      if (locate(r, local, incl, sp, g, vg, r2)) {
+        const int64_t i0 = g * kSubTile;
+        uint32_t *b = buf + warp * kSubTile;
+        for (int q = lane; q < kSubTile / 4; q += 32) {
+          const int64_t i = i0 + 4 * q;
+          uint4 x = make_uint4(0, 0, 0, 0);
+          if (i + 3 < N) x = __ldcg(reinterpret_cast<const uint4 *>(sd.w + i));
+          else {
+            x.x = i < N ? __ldcg(sd.w + i) : 0u;
+            x.y = i + 1 < N ? __ldcg(sd.w + i + 1) : 0u;
+            x.z = i + 2 < N ? __ldcg(sd.w + i + 2) : 0u;
+          }
+          reinterpret_cast<uint4 *>(b)[q] = x;
+        }
+        if (lane == 0) spec_g[warp] = g;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t *__restrict__ wp = sd.w;
+    const uint64_t u_lo = philox_u64(seed, sid, stp, (uint32_t)lane, 0u);
+    const uint64_t u_hi = lane + 32 < k ? philox_u64(seed, sid, stp, (uint32_t)(lane + 32), 0u) : 0ull;
+    int count = 0;
+    for (int j = 0; j < k; ++j) {
+      uint64_t local, incl;
+      const uint64_t W = totals(local, incl);
+      if (W == 0) break;
+      const uint64_t uj = j < 32 ? __shfl_sync(kFullMask, u_lo, j) : __shfl_sync(kFullMask, u_hi, j - 32);
+      const uint64_t r = scaled_draw(uj, W);
+      int64_t sp, g;
+      uint64_t vg, r2;
+      if (!locate(r, local, incl, sp, g, vg, r2)) break;   // cannot happen with consistent sums
+      // the sub-tile's weights: a fetched copy, else from L2
+      int bsel = -1;
+      for (int b = 0; b < kSpec; ++b)
+        if (spec_g[b] == g) {
+          bsel = b;
+          break;
+        }
+      const int64_t i0 = g * kSubTile + lane * 32;
+      uint32_t wv[32];
+      if (bsel >= 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(buf + bsel * kSubTile + lane * 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint4 x = s4[q];
+          wv[4 * q] = x.x;
+          wv[4 * q + 1] = x.y;
+          wv[4 * q + 2] = x.z;
+          wv[4 * q + 3] = x.w;
+        }
+      } else if (i0 + 31 < N) {
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(wp + i0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint4 x = __ldcg(w4 + q);
+          wv[4 * q] = x.x;
+          wv[4 * q + 1] = x.y;
+          wv[4 * q + 2] = x.z;
+          wv[4 * q + 3] = x.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) wv[q] = i0 + q < N ? __ldcg(wp + i0 + q) : 0u;
+      }
+      uint64_t t16[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) t16[q] = (uint64_t)wv[2 * q] + wv[2 * q + 1];
+#pragma unroll
+      for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q) t16[q] = t16[2 * q] + t16[2 * q + 1];
+      const uint64_t ls = t16[0];
+      const uint64_t inc3 = warp_incl(ls);
+      const bool mine = inc3 - ls <= r2 && r2 < inc3;
+      uint64_t acc = inc3 - ls;
+      int qsel = -1;
+      uint32_t wsel = 0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        if (mine && qsel < 0 && r2 < acc + wv[q]) {
+          qsel = q;
+          wsel = wv[q];
+        }
+        acc += wv[q];
+      }
+      if (mine && qsel >= 0) {
+        const int64_t i = i0 + qsel;
+        pick[j] = i;
+        wp[i] = 0;
+        for (int b = 0; b < kSpec; ++b)
+          if (spec_g[b] == g) buf[b * kSubTile + (i - g * kSubTile)] = 0u;
+        if (cached) subc[g] = vg - wsel;
+        else sd.sub_sum[g] = vg - wsel;
+        sup[sp] -= wsel;
+        atomicOr(sd.eval + (i >> 5), 1u << (i & 31));
+      }
+      __syncwarp();
+      ++count;
+    }
+    if (lane == 0) sh_n = count;
+  }
+  __syncthreads();
+  return sh_n;
+}
+
+template <int THREADS, int DT, bool TOPK>
+struct Scorer {
+  static constexpr int NW = THREADS / 32;
+  const SearchDev &sd;
+  int nt, D, L, k;
+  bool first, last;
+  float mn, mx;
+  bool any;
+  uint64_t *tk;          // this warp's top-k list (TOPK)
+
+  // configurations base + c * THREADS + threadIdx.x, c < CPT, below hi
+  template <int CPT>
+  __device__ __forceinline__ void chunk(int64_t base, int64_t hi) {
+    const uint32_t *__restrict__ narrow_p = sd.narrow;
+    const uint32_t *__restrict__ eval_p = sd.eval;
+    float *__restrict__ s_p = sd.s;
+    uint32_t W[CPT];
+    float s[CPT];
+    bool ok[CPT];
+    uint32_t ev[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int64_t i = base + (int64_t)c * THREADS + threadIdx.x;
+      ok[c] = i < hi;
+      W[c] = ok[c] ? __ldg(narrow_p + i) : 0u;
+      s[c] = (first || !ok[c]) ? 0.0f : __ldcg(s_p + i);
+      ev[c] = (last && ok[c]) ? (__ldg(eval_p + (i >> 5)) >> (i & 31)) & 1u : 0u;
+    }
+    walk_trees<DT, CPT>(nt, D, L, W, s);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int64_t i = base + (int64_t)c * THREADS + threadIdx.x;
+      if (!last) {
+        if (ok[c]) __stcg(s_p + i, s[c]);
+        continue;
+      }
+      const bool live = ok[c] && !ev[c];
+      if (ok[c]) __stcg(s_p + i, live ? s[c] : 0.0f);
+      if (live) {
+        mn = fminf(mn, s[c]);
+        mx = fmaxf(mx, s[c]);
+        any = true;
+      }
+      if constexpr (TOPK) key_offer(tk, k, live, live ? topk_key(s[c], (uint32_t)i) : 0ull);
+    }
+  }
+
+  // the range [lo, hi): full chunks of CPT configurations per thread, then
+  // the remainder with fewer per thread
+  template <int CPT>
+  __device__ __forceinline__ void range(int64_t lo, int64_t hi) {
+    int64_t base = lo;
+    constexpr int64_t full = (int64_t)THREADS * CPT;
+    for (; base + full <= hi; base += full) chunk<CPT>(base, hi);
+    if constexpr (CPT >= 4) {
+      constexpr int64_t half = (int64_t)THREADS * (CPT / 2);
+      if (base + half <= hi) {
+        chunk<CPT / 2>(base, hi);
+        base += half;
+      }
+    }
+    if constexpr (CPT >= 2) {
+      constexpr int64_t two = (int64_t)THREADS * 2;
+      for (; base + two <= hi; base += two) chunk<2>(base, hi);
+    }
+    for (; base < hi; base += THREADS) chunk<1>(base, hi);
+  }
+};
+
+template <int THREADS, int CPT, int DT, bool TOPK>
+__global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant__ FusedArgs fa) {
+  uint8_t *smem = fz_smem;
+  constexpr int NW = THREADS / 32;
+  constexpr int kListBytes = NW * KTUNE_MAX_K * 8;
+  __shared__ float sh_A[KTUNE_MAX_COUNTERS], sh_dl[KTUNE_MAX_COUNTERS];
+  __shared__ int sh_active[KTUNE_MAX_COUNTERS];
+  __shared__ int sh_nact, sh_ok, sh_last;
+  __shared__ float red_mn[NW], red_mx[NW];
+  __shared__ int sh_any[NW];
+  const SearchDev &sd = *fa.srch;
+  const StepDev &st = fa.st;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned G = gridDim.x;
+  const int K = sd.K, D = DT > 0 ? DT : sd.D, L = 1 << D;
+  const int64_t N = sd.N;
+  const int k = st.k;
+
+  // ---- P0: c_profile's prediction per counter, the active counters ----------------
+  if (warp == 0) {
+    const uint32_t plo = (uint32_t)st.cprof_packed, phi = (uint32_t)(st.cprof_packed >> 32);
+    for (int p = lane; p < K; p += 32) {
+      const uint8_t *nd = sd.nodes + (size_t)p * L;
+      uint32_t i = 0;
+      for (int l = 0; l < D; ++l) i = tree_step(i, __ldg(nd + i), plo, phi);
+      sh_A[p] = __ldg(sd.leaves + (size_t)p * L + (i - (uint32_t)(L - 1)));
+      sh_dl[p] = st.delta[p];
+    }
+    __syncwarp();
+    int base = 0;
+    for (int q0 = 0; q0 < K; q0 += 32) {
+      const int q = q0 + lane;
+      const bool act = q < K && sh_dl[q] != 0.0f && sh_A[q] != 0.0f;
+      const unsigned m = __ballot_sync(kFullMask, act);
+      if (act) sh_active[base + __popc(m & ((1u << lane) - 1u))] = q;
+      base += __popc(m);
+    }
+    if (lane == 0) sh_nact = base;
+  }
+  __syncthreads();
+  const int n_active = sh_nact;
+  if (blockIdx.x == 0) {
+    for (int p = threadIdx.x; p < K; p += THREADS) {
+      sd.pcprof[p] = sh_A[p];
+      sd.delta[p] = sh_dl[p];
+    }
+    if (threadIdx.x == 0) *sd.n_active = n_active;
+    if (!TOPK) {   // super-tile sums are accumulated in P2, after the barrier
+      const int64_t n_super = ((N + kSubTile - 1) / kSubTile + kSuper - 1) / kSuper;
+      for (int64_t i = threadIdx.x; i < n_super; i += THREADS) sd.super_sum[i] = 0;
+    }
+  }
+
+  // ---- P1: score this CTA's range ------------------------------------------------
+  const int64_t lo = N * (int64_t)blockIdx.x / G, hi = N * (int64_t)(blockIdx.x + 1) / G;
+  const int tree_words = 2 * L;
+  const int budget = kFusedSmem - (TOPK ? kListBytes : 0);
+  const int per_group = max(1, budget / (tree_words * 4));
+  const int n_groups = max(1, (n_active + per_group - 1) / per_group);
+  uint32_t *trees = reinterpret_cast<uint32_t *>(smem);
+  uint64_t *lists = reinterpret_cast<uint64_t *>(smem + kFusedSmem - kListBytes);
+  Scorer<THREADS, DT, TOPK> sc{sd, 0, D, L, k, true, false, FLT_MAX, -FLT_MAX, false,
+                               lists + warp * KTUNE_MAX_K};
+  if (TOPK)
+    for (int e = lane; e < KTUNE_MAX_K; e += 32) sc.tk[e] = 0ull;
+  for (int g = 0; g < n_groups; ++g) {
+    const int t0 = g * per_group;
+    const int nt = max(0, min(per_group, n_active - t0));
+    __syncthreads();   // the previous group's walks are done
+    // node words by asynchronous copies, then the summands from the leaf values
+    for (int a = 0; a < nt; ++a) {
+      const int p = sh_active[t0 + a];
+      if (L >= 4) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(fa.words + (size_t)p * L);
+        uint4 *dst = reinterpret_cast<uint4 *>(trees + (size_t)a * tree_words);
+        for (int i = threadIdx.x; i < L / 4; i += THREADS) cp_async16(dst + i, src + i);
+      } else {
+        for (int i = threadIdx.x; i < L; i += THREADS)
+          trees[(size_t)a * tree_words + i] = __ldg(fa.words + (size_t)p * L + i);
+      }
+    }
+    for (int a = 0; a < nt; ++a) {
+      const int p = sh_active[t0 + a];
+      const float A = sh_A[p], dl = sh_dl[p];
+      const float *lv = sd.leaves + (size_t)p * L;
+      float *terms = reinterpret_cast<float *>(trees + (size_t)a * tree_words + L);
+      for (int i = threadIdx.x; i < L; i += THREADS) {
+        const float x = __ldg(lv + i);
+        const float den = __fadd_rn(x, A);
+        float t = 0.0f;
+        if (x != 0.0f && den != 0.0f) t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(x, A), den));
+        terms[i] = t;
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    sc.nt = nt;
+    sc.first = g == 0;
+    sc.last = g == n_groups - 1;
+    if (lo < hi) sc.template range<CPT>(lo, hi);
+  }
+  // CTA minimum / maximum of the unevaluated scores
+  {
+    float mn = sc.mn, mx = sc.mx;
+    for (int o = 16; o; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(kFullMask, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(kFullMask, mx, o));
+    }
+    const bool wany = __any_sync(kFullMask, sc.any);
+    if (lane == 0) {
+      red_mn[warp] = mn;
+      red_mx[warp] = mx;
+      sh_any[warp] = wany;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = INFINITY, b = -INFINITY;
+      for (int w = 0; w < NW; ++w)
+        if (sh_any[w]) {
+          a = fminf(a, red_mn[w]);
+          b = fmaxf(b, red_mx[w]);
+        }
+      if (a <= b) {
+        atomicMin(fa.mm_live, okey(a));
+        atomicMax(fa.mm_live + 1, okey(b));
+      }
+    }
+  }
+  if constexpr (TOPK) {
+    // this CTA's k best, merged from its warps' lists, for the last CTA
+    __syncthreads();
+    if (warp == 0) warp_merge(lists, NW, KTUNE_MAX_K, k, fa.cand + (size_t)blockIdx.x * KTUNE_MAX_K);
+  } else {
+    // ---- grid barrier: s_min and s_max are final ------------------------------------
+    if (!grid_barrier(fa.sync, G, fa.wait_ns, &sh_ok) && threadIdx.x == 0)
+      atomicExch(fa.status, KTUNE_ETIMEOUT);
+    fused_weights(fa);
+  }
+
+  // ---- the CTA that finishes last selects ------------------------------------------
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long old = atomicAdd(fa.sync + 1, 1ull);
+    sh_last = ((old + 1) % G) == 0;
+  }
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+
+  __shared__ int64_t pick[KTUNE_MAX_K];
+  __shared__ float pick_s[KTUNE_MAX_K];
+  __shared__ int sh_count;
+  if constexpr (TOPK) {
+    // merge the G CTA lists (each descending) into the k best
+    __shared__ uint64_t best[KTUNE_MAX_K];
+    if (warp == 0) {
+      warp_merge(fa.cand, (int)G, KTUNE_MAX_K, k, best);
+      if (lane == 0) {
+        int c = 0;
+        for (int r = 0; r < k; ++r) {
+          if (best[r] == 0) break;
+          pick[c] = topk_ord(best[r]);
+          pick_s[c] = topk_score(best[r]);
+          ++c;
+        }
+        sh_count = c;
+      }
+    }
+    __syncthreads();
+    const int count = sh_count;
+    if ((int)threadIdx.x < count)
+      atomicOr(sd.eval + (pick[threadIdx.x] >> 5), 1u << (pick[threadIdx.x] & 31));
+  } else {
+    const int count = fused_draws(fa, pick);
+    if (threadIdx.x == 0) sh_count = count;
+    __syncthreads();
+    if ((int)threadIdx.x < count) pick_s[threadIdx.x] = __ldcg(sd.s + pick[threadIdx.x]);
+    __syncthreads();
+  }
+  // outputs; the step's min / max for the statistics; the accumulator reset
+  const int count = sh_count;
+  if ((int)threadIdx.x < count) {
+    const int j = threadIdx.x;
+    const uint64_t p = __ldg(sd.packed + pick[j]);
+    int64_t raw = 0;
+    for (int q = 0; q < sd.sa.P; ++q) raw += (int64_t)nib64(p, q) * sd.sa.stride[q];
+    st.out_raw[j] = raw;
+    st.out_score[j] = pick_s[j];
+    if (st.out_packed) st.out_packed[j] = p;
+  }
+  if (threadIdx.x == 0) {
+    if (st.n_out) *st.n_out = count;
+    sd.mm[0] = __ldcg(fa.mm_live);
+    sd.mm[1] = __ldcg(fa.mm_live + 1);
+    fa.mm_live[0] = INT_MAX;
+    fa.mm_live[1] = INT_MIN;
+  }
+}
+
+// The shared-memory opt-in of one kernel, once per device (the static flag
+// belongs to this kernel's instantiation).
+template <int THREADS, int CPT, int DT, bool TOPK>
+cudaError_t smem_opt_in() {
+  static std::atomic<uint64_t> done{0};   // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load() & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_step_fused<THREADS, CPT, DT, TOPK>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
+  if (e == cudaSuccess && bit) done.fetch_or(bit);
+  return e;
+}
+
+template <int THREADS, int CPT, int DT, bool TOPK>
+cudaError_t launch_fused_t(const FusedArgs &fa, int grid, cudaStream_t st) {
+  auto kern = k_step_fused<THREADS, CPT, DT, TOPK>;
+  cudaError_t e = smem_opt_in<THREADS, CPT, DT, TOPK>();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = kFusedSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, fa);
+}
+
+template <int THREADS, int CPT, bool TOPK>
+cudaError_t launch_fused_d(const FusedArgs &fa, int D, int grid, cudaStream_t st) {
+  switch (D) {
+    case 12: return launch_fused_t<THREADS, CPT, 12, TOPK>(fa, grid, st);
+    case 8: return launch_fused_t<THREADS, CPT, 8, TOPK>(fa, grid, st);
+    default: return launch_fused_t<THREADS, CPT, 0, TOPK>(fa, grid, st);
+  }
+}
+
+template <int THREADS, int CPT, int DT, bool TOPK>
+int blocks_per_sm_t() {
+  int b = 0;
+  auto kern = k_step_fused<THREADS, CPT, DT, TOPK>;
+  if (smem_opt_in<THREADS, CPT, DT, TOPK>() != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, THREADS, kFusedSmem) != cudaSuccess) return 0;
+  return b;
+}
+
+}  // namespace
+
+// Shapes of the fused kernel: (CTA threads, configurations per thread per chunk).
+static const int kFusedShapes[][2] = {{512, 8}, {1024, 4}, {1024, 8}};
+
+int fused_shapes() { return (int)(sizeof(kFusedShapes) / sizeof(kFusedShapes[0])); }
+
+int fused_blocks_per_sm(int shape) {
+  switch (shape) {
+    case 1: return blocks_per_sm_t<1024, 4, 0, false>();
+    case 2: return blocks_per_sm_t<1024, 8, 0, false>();
+    default: return blocks_per_sm_t<512, 8, 0, false>();
+  }
+}
+
+cudaError_t launch_step_fused(const FusedArgs &fa, int shape, bool topk, int D, int grid,
+                              cudaStream_t st) {
+  switch (shape) {
+    case 1:
+      return topk ? launch_fused_d<1024, 4, true>(fa, D, grid, st) : launch_fused_d<1024, 4, false>(fa, D, grid, st);
+    case 2:
+      return topk ? launch_fused_d<1024, 8, true>(fa, D, grid, st) : launch_fused_d<1024, 8, false>(fa, D, grid, st);
+    default:
+      return topk ? launch_fused_d<512, 8, true>(fa, D, grid, st) : launch_fused_d<512, 8, false>(fa, D, grid, st);
+  }
+}
+
+// Node words of the one-word walk for every node of K padded trees: word 0
+// of each tree unused, word i + 1 for node i (1-based heap).
+__global__ void k_fused_words(const uint8_t *__restrict__ nodes, int K, int D, PrepArgs lay,
+                              uint32_t *__restrict__ words) {
+  const int L = 1 << D;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)K * L) return;
+  const int i = (int)(g % L);
+  const uint32_t nb = nodes[g];
+  uint32_t w = 0;
+  if (i + 1 < L) {
+    const int f = nb >> 4, t = nb & 15;
+    const int wd = lay.width[f];
+    const uint32_t sh = 32u - lay.pos[f] - wd;
+    uint32_t c8 = 0;
+    if (t < lay.radix[f] - 1) c8 = 255u - ((((uint32_t)t + 1u) << (8 - wd)) - 1u);
+    w = (c8 << 24) | sh;
+    words[g + 1] = w;
+  } else {
+    words[g - i] = 0;   // word 0 of the tree
+  }
+}
+
+cudaError_t launch_fused_words(const uint8_t *nodes, int K, int D, const PrepArgs &lay,
+                               uint32_t *words, cudaStream_t st) {
+  const int64_t n = (int64_t)K << D;
+  k_fused_words<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nodes, K, D, lay, words);
+  return cudaGetLastError();
+}
+
+}  // namespace ktune

@@ -138,6 +138,99 @@ __device__ __forceinline__ uint32_t narrow_visit(uint32_t j, uint32_t word, uint
   return j;
 }
 
+// ---- ordered keys, evaluated bits, top-k lists, scans ----------------------
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Ordered-int key of a float (monotone: a < b iff okey(a) < okey(b)), for
+// min / max by integer atomics, and its inverse.
+__device__ __forceinline__ int okey(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float okey_inv(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
+
+// Top-k key: larger is better (higher score, then lower ordinal).
+__device__ __forceinline__ uint64_t topk_key(float s, uint32_t ord) {
+  uint32_t u = __float_as_uint(s);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((uint64_t)u << 32) | (0xFFFFFFFFu - ord);
+}
+__device__ __forceinline__ float topk_score(uint64_t key) {
+  const uint32_t u = (uint32_t)(key >> 32);
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+__device__ __forceinline__ uint32_t topk_ord(uint64_t key) { return 0xFFFFFFFFu - (uint32_t)key; }
+
+
+__device__ __forceinline__ bool is_ev(const uint32_t *ev, int64_t i) { return (ev[i >> 5] >> (i & 31)) & 1u; }
+
+// ---- top-k lists ------------------------------------------------------------------
+// Per-warp descending list of up to k keys (0 = empty) with their raw indices.
+__device__ __forceinline__ void warp_insert(uint64_t *key, int64_t *raw, int k, uint64_t kk,
+                                            int64_t rr) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t a = lane < k ? key[lane] : 0ull;
+  const uint64_t b = lane + 32 < k ? key[lane + 32] : 0ull;
+  const int p = __popc(__ballot_sync(kFullMask, a > kk)) + __popc(__ballot_sync(kFullMask, b > kk));
+  if (p >= k) return;
+  const uint64_t pa = (lane >= 1 && lane - 1 < k) ? key[lane - 1] : 0ull;
+  const int64_t pra = (lane >= 1 && lane - 1 < k) ? raw[lane - 1] : 0;
+  const uint64_t pb = (lane + 31 < k) ? key[lane + 31] : 0ull;
+  const int64_t prb = (lane + 31 < k) ? raw[lane + 31] : 0;
+  __syncwarp();
+  if (lane < k && lane >= p) {
+    key[lane] = lane == p ? kk : pa;
+    raw[lane] = lane == p ? rr : pra;
+  }
+  if (lane + 32 < k && lane + 32 >= p) {
+    key[lane + 32] = lane + 32 == p ? kk : pb;
+    raw[lane + 32] = lane + 32 == p ? rr : prb;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void topk_offer(uint64_t *key, int64_t *raw, int k, bool ok, uint64_t kk,
+                                           int64_t rr) {
+  const uint64_t theta = key[k - 1];
+  unsigned m = __ballot_sync(kFullMask, ok && kk > theta);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const uint64_t k2 = __shfl_sync(kFullMask, kk, src);
+    const int64_t r2 = __shfl_sync(kFullMask, rr, src);
+    warp_insert(key, raw, k, k2, r2);
+  }
+}
+
+
+template <typename T>
+__device__ __forceinline__ T warp_incl(T v) {
+  const int lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = __shfl_up_sync(kFullMask, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Inclusive scan over the block; *total = block sum.  Uses sh[32].
+template <typename T>
+__device__ T block_incl(T v, T *sh, T *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T incl = warp_incl(v);
+  __syncthreads();
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const T x = lane < nw ? sh[lane] : (T)0;
+    sh[lane] = warp_incl(x);
+  }
+  __syncthreads();
+  *total = sh[nw - 1];
+  return (warp ? sh[warp - 1] : (T)0) + incl;
+}
+
+
 // ---- normalisation and weights ---------------------------------------------
 // Eq. score_normalization in float32, each operation rounded, x^8 as
 // ((x^2)^2)^2, s = 0 mapped to 1; weight = round-half-even(s_norm * 2^20).

@@ -73,6 +73,7 @@ _SIGS = {
     "ktune_search_set_cached": ([_vp, C.c_int], C.c_int),
     "ktune_search_set_neighbourhood": ([_vp, C.c_int], C.c_int),
     "ktune_search_scores_device": ([_vp, C.c_int64, C.c_int64, _vp, _vp, _vp], C.c_int),
+    "ktune_search_set_fused": ([_vp, C.c_int], C.c_int),
     "ktune_search_save": ([_vp, _vp, C.POINTER(C.c_size_t)], C.c_int),
     "ktune_search_load": ([_vp, _vp, _vp, C.c_size_t, _vp, C.POINTER(_vp)], C.c_int),
     "ktune_batch_create": ([C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)], C.c_int),
@@ -316,6 +317,11 @@ class Search:
         """Restrict later steps to c_profile's Hamming neighbourhood (0: off)."""
         check(lib.ktune_search_set_neighbourhood(self.h, int(radius)),
               "ktune_search_set_neighbourhood")
+
+    def set_fused(self, shape: int = 1):
+        """0: four kernels per step; 1..3: the whole step as one persistent
+        kernel of that shape (ktune_search_set_fused)."""
+        check(lib.ktune_search_set_fused(self.h, int(shape)), "ktune_search_set_fused")
 
     def scores_device(self, first: int, count: int, scores_ptr: int = 0, weights_ptr: int = 0,
                       stream=None):

@@ -94,11 +94,14 @@ def synthetic(desc, roles, seed):
 
 
 def run(kt, desc, model, steps, k=5, seed=0, select="sample", flags=0, fseed=0, cached=False,
-        stream=None, valid=None, pred=None, zero_evaluated=True, gpu_model=None, space=None):
+        stream=None, valid=None, pred=None, zero_evaluated=True, gpu_model=None, space=None,
+        fused=None):
     sel = kt.KTUNE_SELECT_TOPK if select == "topk" else kt.KTUNE_SELECT_SAMPLE
     sp = space or kt.Space.from_desc(desc, flags=flags)
     m = gpu_model or kt.Model(sp, model)
     s = kt.Search(sp, m, k=k, seed=seed, select=sel, stream=stream)
+    if fused is not None:
+        s.set_fused(fused)
     if cached:
         s.set_cached(True)
     o = osearch.OracleSearch(desc, model, k=k, seed=seed, mode=select, valid=valid, pred=pred)
@@ -116,24 +119,35 @@ def run(kt, desc, model, steps, k=5, seed=0, select="sample", flags=0, fseed=0, 
     return s, o
 
 
-# ---- fused tree steps ---------------------------------------------------------------
-def test_every_score_and_weight_full_mid_space(kt):
-    """The headline workload: 2.26M configurations, 32 counters, depth-12
-    trees (two groups of active trees in shared memory), k = 5, three steps."""
+# ---- whole-space tree steps ----------------------------------------------------------
+@pytest.fixture(scope="module")
+def mid_trees():
     d = W.load_space("mid_12p")
     roles = W.layout(32)
     model = random_model(d.radices, roles, depth=12, seed=12)
     valid = ospace.enumerate_valid(d)
     pred = otrees.predict(model, ospace.decode(d.radices, valid))
-    run(kt, d, model, steps=3, valid=valid, pred=pred)
+    return d, model, valid, pred
 
 
-def test_every_score_and_weight_graph_path(kt):
+@pytest.mark.parametrize("fused", [1, 0, 2, 3])
+def test_every_score_and_weight_full_mid_space(kt, mid_trees, fused):
+    """The headline workload: 2.26M configurations, 32 counters, depth-12
+    trees (two groups of active trees in shared memory), k = 5, three steps;
+    the whole step as one persistent kernel (each shape) and as four kernels."""
+    d, model, valid, pred = mid_trees
+    run(kt, d, model, steps=3, valid=valid, pred=pred, fused=fused)
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_every_score_and_weight_stream_path(kt, fused):
+    """On a non-default stream: a captured graph of four kernels, or the
+    fused kernel launched directly."""
     import torch
     d = W.load_space("batch_4")
     roles = W.layout(40)
     model = random_model(d.radices, roles, depth=12, seed=41)
-    run(kt, d, model, steps=4, k=7, seed=2, stream=torch.cuda.Stream(), fseed=3)
+    run(kt, d, model, steps=4, k=7, seed=2, stream=torch.cuda.Stream(), fseed=3, fused=fused)
 
 
 def test_every_score_and_weight_tiny_fitted(kt):
@@ -147,12 +161,15 @@ def test_every_score_and_weight_tiny_fitted(kt):
     run(kt, d, model, steps=40, seed=1, valid=valid, fseed=1)
 
 
-@pytest.mark.parametrize("name,K,depth,k", [("batch_2", 32, 10, 16), ("batch_7", 40, 12, 64)])
-def test_every_score_topk(kt, name, K, depth, k):
+@pytest.mark.parametrize("name,K,depth,k,fused", [("batch_2", 32, 10, 16, None),
+                                                   ("batch_7", 40, 12, 64, None),
+                                                   ("batch_7", 40, 12, 64, 0),
+                                                   ("mid_12p", 32, 12, 16, 2)])
+def test_every_score_topk(kt, name, K, depth, k, fused):
     d = W.load_space(name)
     roles = W.layout(K)
     model = random_model(d.radices, roles, depth=depth, seed=k + 1)
-    run(kt, d, model, steps=4, k=k, seed=5, select="topk", fseed=6)
+    run(kt, d, model, steps=3, k=k, seed=5, select="topk", fseed=6, fused=fused)
 
 
 def test_every_score_and_weight_general_walk(kt):
@@ -205,12 +222,8 @@ def test_readback_rules(kt):
 
 
 # ---- cached predictions ----------------------------------------------------------------
-def test_cached_trees_full_mid_space_against_oracle(kt):
-    d = W.load_space("mid_12p")
-    roles = W.layout(32)
-    model = random_model(d.radices, roles, depth=12, seed=13)
-    valid = ospace.enumerate_valid(d)
-    pred = otrees.predict(model, ospace.decode(d.radices, valid))
+def test_cached_trees_full_mid_space_against_oracle(kt, mid_trees):
+    d, model, valid, pred = mid_trees
     run(kt, d, model, steps=3, valid=valid, pred=pred, cached=True, fseed=2)
 
 

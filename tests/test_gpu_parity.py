@@ -172,8 +172,8 @@ def _check(out, K_bound=None):
         np.testing.assert_array_equal(g_sc, o_sc)
 
 
-@pytest.mark.parametrize("seed", range(3))
-def test_steps_tiny_fitted_model(kt, seed):
+@pytest.mark.parametrize("seed,fused", [(0, None), (1, None), (2, None), (0, 0)])
+def test_steps_tiny_fitted_model(kt, seed, fused):
     d = W.space_tiny_block_tile()
     roles = W.layout(16)
     gpu, cnt, rt = _synthetic(d, roles, seed)
@@ -181,17 +181,19 @@ def test_steps_tiny_fitted_model(kt, seed):
     dig = ospace.decode(d.radices, valid)
     samp = sample_indices(len(valid), 0.10, seed)
     model = otrees.fit_model(dig[samp], gpu.evaluate(dig[samp])[0], 8, d.radices, roles)
-    out = run_pair(d, model, cnt, steps=40, seed=seed, valid=valid, runtime_fn=rt, kt=kt)
+    out = run_pair(d, model, cnt, steps=40, seed=seed, valid=valid, runtime_fn=rt, kt=kt,
+                   fused=fused)
     _check(out)
 
 
-@pytest.mark.parametrize("K,depth", [(16, 6), (32, 12), (40, 12)])
-def test_steps_random_trees(kt, K, depth):
+@pytest.mark.parametrize("K,depth,fused", [(16, 6, None), (32, 12, None), (40, 12, None),
+                                           (40, 12, 0), (32, 1, None), (24, 14, 2)])
+def test_steps_random_trees(kt, K, depth, fused):
     d = W.load_space("batch_2")
-    roles = W.layout(K)
+    roles = W.layout(K) if K in (16, 32, 40) else W.layout(40)[:K]
     model = random_model(d.radices, roles, depth=depth, seed=K)
     gpu, cnt, rt = _synthetic(d, roles, 3)
-    out = run_pair(d, model, cnt, steps=12, k=7, seed=11, runtime_fn=rt, kt=kt)
+    out = run_pair(d, model, cnt, steps=12, k=7, seed=11, runtime_fn=rt, kt=kt, fused=fused)
     _check(out)
 
 
@@ -347,8 +349,9 @@ def test_large_on_the_fly_top16_full_size(kt):
 
 @pytest.mark.parametrize("select", ["sample", "topk"])
 def test_graph_path_matches_plain_launches(kt, select):
-    """Steps on a non-default stream run as a captured CUDA graph whose step
-    parameters are replaced each step; they must equal plain launches."""
+    """With four kernels per step (ktune_search_set_fused(0)), steps on a
+    non-default stream run as a captured CUDA graph whose step parameters are
+    replaced each step; they must equal plain launches."""
     import torch
     d = W.load_space("batch_4")
     roles = W.layout(32)
@@ -360,6 +363,7 @@ def test_graph_path_matches_plain_launches(kt, select):
         sp = kt.Space.from_desc(d)
         m = kt.Model(sp, model)
         s = kt.Search(sp, m, k=6, seed=4, select=sel, stream=stream)
+        s.set_fused(0)
         seq = []
         for i in range(6):
             if i == 3:
@@ -371,3 +375,50 @@ def test_graph_path_matches_plain_launches(kt, select):
         assert st.n_kernels == 4 and st.kernel_ms[1] > 0
         runs.append(seq)
     assert runs[0] == runs[1]
+
+
+@pytest.mark.parametrize("select", ["sample", "topk"])
+def test_fused_step_matches_four_kernels(kt, select):
+    """The whole step as one persistent kernel (every shape, default and
+    non-default streams) against the four-kernel chain: the same selections
+    and scores, step after step; one timed kernel per fused step."""
+    import torch
+    d = W.load_space("batch_4")
+    roles = W.layout(40)
+    model = random_model(d.radices, roles, depth=12, seed=18)
+    gpu, cnt, rt = _synthetic(d, roles, 4)
+    sel = kt.KTUNE_SELECT_TOPK if select == "topk" else kt.KTUNE_SELECT_SAMPLE
+    runs = []
+    for shape, stream in [(0, None), (1, None), (2, torch.cuda.Stream()), (3, None)]:
+        sp = kt.Space.from_desc(d)
+        m = kt.Model(sp, model)
+        s = kt.Search(sp, m, k=9, seed=6, select=sel, stream=stream)
+        s.set_fused(shape)
+        s.set_timing(True)
+        seq = []
+        for _ in range(5):
+            raw, sc = s.step(cnt(s.current()))
+            seq.append((list(raw), list(sc)))
+            s.report(rt(raw))
+        st = s.stats()
+        assert st.n_kernels == (4 if shape == 0 else 1) and st.kernel_ms[0] > 0
+        runs.append(seq)
+    for r in runs[1:]:
+        assert r == runs[0]
+
+
+def test_fused_step_refused_where_it_does_not_apply(kt):
+    values = [[1, 2, 3, 4, 5]] * 11           # 33 bits: the two-word walk
+    d = W.SpaceDesc("wide", ["p%d" % j for j in range(11)], values, [])
+    sp = kt.Space.from_desc(d)
+    s = kt.Search(sp, kt.Model(sp, random_model(d.radices, W.layout(16), depth=5, seed=1)), k=5)
+    with pytest.raises(kt.KtuneError) as e:
+        s.set_fused(1)
+    assert e.value.code == kt.KTUNE_ESTATE
+    s.set_fused(0)
+    d2 = W.load_space("batch_2")
+    sp2 = kt.Space.from_desc(d2)
+    s2 = kt.Search(sp2, kt.Model(sp2, random_model(d2.radices, W.layout(16), depth=5, seed=1)), k=5)
+    with pytest.raises(kt.KtuneError) as e:
+        s2.set_fused(7)
+    assert e.value.code == kt.KTUNE_EINVAL
