@@ -220,7 +220,7 @@ def timed_device_steps(kt, torch, s, traj, lo, hi, k, stream, flush):
     out_sc = torch.empty(k, dtype=torch.float32, device="cuda")
     n_out = torch.empty(1, dtype=torch.int32, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    step_ms, kern_ms, visits, scored, n_active = [], np.zeros(4), 0, 0, []
+    step_ms, kern_ms, visits, scored, n_active = [], np.zeros(8), 0, 0, []
     for i in range(lo, hi):
         flush.zero_()
         s.set_profile(int(traj[i][0]))
@@ -230,7 +230,7 @@ def timed_device_steps(kt, torch, s, traj, lo, hi, k, stream, flush):
         e1.record(stream)
         st = s.stats()                  # synchronises
         step_ms.append(e0.elapsed_time(e1))
-        kern_ms += np.array(st.kernel_ms[:4])
+        kern_ms += np.array(st.kernel_ms[:8])
         visits += st.n_scored * st.n_active * (st.depth + 1)
         scored += st.n_scored
         n_active.append(st.n_active)
@@ -405,8 +405,12 @@ def headline_roofline(fused, kern_ms, achieved, peak_visits, props, sm_mhz, src)
         r["kernel"] = ("k_step_fused (the whole step: c_profile prediction, tree walk + Eq. score, "
                        "weights, draws; shape %d)" % fused)
         r["traffic"] = PROFILED_TRAFFIC.get("k_step_fused")
+        tot = kern_ms[0]
+        names = ("predict_cprofile", "summands_barrier", "walk", "barrier_wait", "weights",
+                 "last_cta_slack", "draws")
+        r["phase_share"] = {n: kern_ms[1 + i] / tot for i, n in enumerate(names)}
     else:
-        tot = kern_ms.sum()
+        tot = kern_ms[:4].sum()
         r["kernel"] = "k_bscore (tree walk + Eq. score)"
         r["traffic"] = PROFILED_TRAFFIC["k_bscore"]
         r["kernel_share"] = {"prepare": kern_ms[0] / tot, "score": kern_ms[1] / tot,
@@ -1036,7 +1040,7 @@ def main():
     ap.add_argument("--mlp-train-steps", type=int, default=2000,
                     help="Adam steps (4096 rows each) of the MLP path's training")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fused", type=int, default=1,
+    ap.add_argument("--fused", type=int, default=2,
                     help="step shape of the headline search (ktune_search_set_fused): 0 = four "
                          "kernels, 1..3 = the whole step as one persistent kernel")
     args = ap.parse_args()

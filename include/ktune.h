@@ -293,16 +293,23 @@ int ktune_search_set_neighbourhood(ktune_search *search, int radius);
  * bounded: a wait that gives up makes the step return KTUNE_ETIMEOUT), then
  * its warps compute the integer weights of one sub-tile each, and the CTA that
  * finishes last makes the draws (or merges the top-k lists).  Both give the
- * same scores, weights and selections bit for bit.  Shape 1 is the default for
+ * same scores, weights and selections bit for bit.  Shape 2 is the default for
  * the searches it applies to; other searches refuse shapes > 0 (KTUNE_ESTATE).
  * Cached predictions and neighbourhood-restricted steps keep their own
  * kernels.  Synchronises the search's last stream. */
 int ktune_search_set_fused(ktune_search *search, int shape);
 
 /* Statistics of the most recent step.  kernel_ms holds the device time of
- * each kernel of that step in launch order (prepare, score, weights, select;
- * one entry for a fused step), measured with CUDA events on the step's
- * stream, only while timing is enabled by ktune_search_set_timing (else 0).
+ * each kernel of that step in launch order (prepare, score, weights, select),
+ * measured with CUDA events on the step's stream, only while timing is
+ * enabled by ktune_search_set_timing (else 0).  A fused step has one kernel
+ * (n_kernels = 1, kernel_ms[0]); kernel_ms[1..7] then hold its phases
+ * (device global timer): as seen by CTA 0, c_profile's prediction, the
+ * per-leaf summands and the first grid barrier, the walk of CTA 0's range,
+ * the wait at the second grid barrier, the weights of CTA 0's share; then
+ * the time from CTA 0's completion to that of the last CTA, and the draws made
+ * by that CTA (the top-k form has no second barrier and no weights: its walk
+ * phase runs up to CTA 0's completion).
  * Synchronises the stream of the last step; returns KTUNE_ETIMEOUT (with the
  * statistics filled in) when a barrier wait of that fused step gave up. */
 typedef struct {

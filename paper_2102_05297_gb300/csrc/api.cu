@@ -1017,7 +1017,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   h->cprof_raw = raw;
   h->cprof_packed = host_pack(s, raw);
   h->n_evaluated = 1;
-  if (m->kind == 1 && h->mode == 0 && fused_blocks_per_sm(0) >= 1) {
+  const int fshape = fused_blocks_per_sm(1) >= 1 ? 2 : fused_blocks_per_sm(0) >= 1 ? 1 : 0;
+  if (m->kind == 1 && h->mode == 0 && fshape) {
     // the whole step as one persistent kernel (the default where it applies)
     const int L = 1 << m->D;
     h->fused_grid = h->num_sms;
@@ -1028,7 +1029,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
       lay.radix[j] = (uint8_t)s->sa.radix[j];
     }
     const int mm0[2] = {INT_MAX, INT_MIN};
-    if ((rc = dalloc(&h->d_fz_words, (size_t)m->K * L)) || (rc = dalloc(&h->d_fz_mm, 2)) ||
+    if ((rc = dalloc(&h->d_fz_words, (size_t)m->K * L)) || (rc = dalloc(&h->d_fz_terms, (size_t)m->K * L)) ||
+        (rc = dalloc(&h->d_fz_mm, 2)) || (rc = dalloc(&h->d_fz_phase, 8)) ||
         (rc = dalloc(&h->d_fz_sync, 2)) || (rc = dalloc(&h->d_fz_status, 1)) ||
         (rc = dalloc(&h->d_fz_cand, (size_t)h->fused_grid * KTUNE_MAX_K)))
       return fail(rc);
@@ -1040,7 +1042,7 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
       set_error("fused-step set-up failed");
       return fail(KTUNE_ECUDA);
     }
-    h->fused = 1;
+    h->fused = fshape;
   }
   *out = h;
   return KTUNE_OK;
@@ -1060,7 +1062,7 @@ int ktune_search_destroy(ktune_search *h) {
   cudaFree(h->d_nbr_buf);
   cudaFree(h->d_cache);
   cudaFree(h->d_leaf_cache);
-  void *fz[] = {h->d_fz_words, h->d_fz_mm, h->d_fz_sync, h->d_fz_status, h->d_fz_cand};
+  void *fz[] = {h->d_fz_words, h->d_fz_terms, h->d_fz_phase, h->d_fz_mm, h->d_fz_sync, h->d_fz_status, h->d_fz_cand};
   for (void *p : fz) cudaFree(p);
   void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
                  h->d_s, h->d_w, h->d_subsum, h->d_supsum, h->d_cand_key, h->d_cand_raw, h->d_mm, h->d_srch,
@@ -1238,11 +1240,13 @@ static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *
     FusedArgs fa{};
     fa.srch = h->d_srch;
     fa.words = h->d_fz_words;
+    fa.terms = h->d_fz_terms;
     fa.mm_live = h->d_fz_mm;
     fa.sync = h->d_fz_sync;
     fa.status = h->d_fz_status;
     fa.cand = h->d_fz_cand;
     fa.wait_ns = 1000000000ull;
+    fa.phase_ns = h->timing ? h->d_fz_phase : nullptr;
     fa.st = sp;
     if (h->timing) CK(cudaEventRecord(h->ev[0], st));
     CK(launch_step_fused(fa, h->fused - 1, h->opts.select == KTUNE_SELECT_TOPK, h->model->D,
@@ -1612,6 +1616,15 @@ int ktune_search_stats(ktune_search *h, ktune_step_stats *out) {
   if (h->timing && h->last_fused) {
     out->n_kernels = 1;
     CK(cudaEventElapsedTime(&out->kernel_ms[0], h->ev[0], h->ev[1]));
+    // the fused kernel's phases, from its time stamps
+    uint64_t t[8];
+    CK(cudaMemcpy(t, h->d_fz_phase, sizeof(t), cudaMemcpyDeviceToHost));
+    const bool sample = h->opts.select == KTUNE_SELECT_SAMPLE;
+    const uint64_t end_p1 = sample ? t[3] : t[5];
+    const double ph[7] = {(double)(t[1] - t[0]), (double)(t[2] - t[1]), (double)(end_p1 - t[2]),
+                          sample ? (double)(t[4] - t[3]) : 0.0, sample ? (double)(t[5] - t[4]) : 0.0,
+                          (double)((int64_t)(t[6] - t[5])), (double)(t[7] - t[6])};
+    for (int i = 0; i < 7; ++i) out->kernel_ms[1 + i] = (float)(ph[i] * 1e-6);
   } else if (h->timing) {
     out->n_kernels = 4;
     for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&out->kernel_ms[i], h->ev[i], h->ev[i + 1]));

@@ -189,11 +189,13 @@ struct StepDev {
 struct FusedArgs {
   const SearchDev *srch;
   const uint32_t *words;          // [K][L] node words of the one-word walk (word 0 of a tree unused)
+  float *terms;                   // [K][L] the step's per-leaf summands, by active rank
   int *mm_live;                   // [2] ordered-int min / max accumulated during the step
   unsigned long long *sync;       // [2] grid-barrier arrivals, completions (only ever grow)
   int *status;                    // KTUNE_ETIMEOUT when a barrier wait gave up
   uint64_t *cand;                 // [grid][KTUNE_MAX_K] per-CTA top-k keys
   uint64_t wait_ns;               // limit of each barrier wait
+  uint64_t *phase_ns;             // [8] phase time stamps (null: none taken)
   StepDev st;
 };
 int fused_shapes();
@@ -514,6 +516,8 @@ struct ktune_search {
   int fused_grid = 0;
   bool last_fused = false;
   uint32_t *d_fz_words = nullptr;      // [K][L] node words
+  float *d_fz_terms = nullptr;         // [K][L] the step's per-leaf summands
+  uint64_t *d_fz_phase = nullptr;      // [8] phase time stamps (timing enabled)
   int *d_fz_mm = nullptr;              // [2] live min / max
   unsigned long long *d_fz_sync = nullptr;
   int *d_fz_status = nullptr;

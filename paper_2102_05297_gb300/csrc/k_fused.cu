@@ -26,6 +26,7 @@
 #include <float.h>
 #include <limits.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "device_common.cuh"
@@ -36,7 +37,7 @@ namespace ktune {
 
 namespace {
 
-constexpr int kFusedSmem = 225 * 1024;   // dynamic shared memory
+constexpr int kFusedSmem = 224 * 1024;   // dynamic shared memory (+ static, within the 227 KB per CTA)
 
 // The kernels of this file address their dynamic shared memory through this
 // array, so that every access derived from it is known to be a shared one.
@@ -50,6 +51,12 @@ __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
+}
+
+// Phase time stamps of the fused step (globaltimer): slot q written by CTA 0
+// (or, for the draws, by the CTA that makes them) when fa.phase_ns is set.
+__device__ __forceinline__ void stamp(const FusedArgs &fa, int q, bool who) {
+  if (fa.phase_ns && who && threadIdx.x == 0) fa.phase_ns[q] = gtimer();
 }
 
 // Every CTA arrives once; returns when all G have arrived, or false after
@@ -164,17 +171,20 @@ __device__ __forceinline__ void walk_trees(int nt, int D, int L, const uint32_t 
   const uint32_t *trees = reinterpret_cast<const uint32_t *>(fz_smem);
   for (int a = 0; a < nt; ++a) {
     const uint32_t *t = trees + a * 2 * L;
+    // the root is the same node for every configuration: one load, then the
+    // remaining levels
+    const uint32_t root = t[1];
     uint32_t j[CPT];
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) j[c] = 1u;
+    for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(1u, root, W[c]);
     if constexpr (DT > 0) {
 #pragma unroll
-      for (int l = 0; l < DT; ++l) {
+      for (int l = 1; l < DT; ++l) {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], t[j[c]], W[c]);
       }
     } else {
-      for (int l = 0; l < D; ++l) {
+      for (int l = 1; l < D; ++l) {
 #pragma unroll
         for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], t[j[c]], W[c]);
       }
@@ -184,52 +194,60 @@ __device__ __forceinline__ void walk_trees(int nt, int D, int L, const uint32_t 
   }
 }
 
-// P2 of the fused step: every warp of the grid, one 1024-configuration
-// sub-tile at a time: Eq. score_normalization over the unevaluated
-// configurations, integer weights, the sub-tile sum and the super-tile sums.
+// P2 of the fused step: every warp of the grid, 512 configurations (half a
+// sub-tile, 16 per lane) at a time: Eq. score_normalization over the
+// unevaluated configurations, the integer weights, their sum added to the
+// sub-tile's (zeroed before the first grid barrier), and to the super-tile's
+// when the draws cannot sum the sub-tiles in shared memory themselves.
 // Out of line, so that its registers do not count against the walk's.
 __device__ __noinline__ void fused_weights(const FusedArgs &fa) {
   const SearchDev &sd = *fa.srch;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
-  const unsigned G = gridDim.x;
   const int64_t N = sd.N;
   const float smin = okey_inv(__ldcg(fa.mm_live)), smax = okey_inv(__ldcg(fa.mm_live + 1));
   const float gm = sd.gamma;
-  const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
-  for (int64_t gsub = (int64_t)blockIdx.x * NW + warp; gsub < n_sub; gsub += (int64_t)G * NW) {
-    const int64_t i0 = gsub * kSubTile;
-    const int64_t ew = (i0 >> 5) + lane;                          // the sub-tile's 32 words
-    const uint32_t evw = ew < ((N + 31) >> 5) ? __ldcg(sd.eval + ew) : 0u;
+  constexpr int kUnit = kSubTile / 2;
+  const int64_t n_units = (N + kUnit - 1) / kUnit;
+  const bool super_here = (N + kSubTile - 1) / kSubTile > kF3Sub;
+  const int64_t eval_words = (N + 31) >> 5;
+  for (int64_t u = (int64_t)blockIdx.x * NW + warp; u < n_units; u += (int64_t)gridDim.x * NW) {
+    const int64_t i0 = u * kUnit;
+    // the unit's 16 evaluated-bit words, lanes 0..15; every load issued first
+    const int64_t ew = (i0 >> 5) + (lane & 15);
+    const uint32_t evw = ew < eval_words ? __ldcg(sd.eval + ew) : 0u;
+    float4 sv[kUnit / 128];
+#pragma unroll
+    for (int q = 0; q < kUnit / 128; ++q) {
+      const int64_t i = i0 + q * 128 + lane * 4;
+      sv[q] = i + 3 < N ? __ldcg(reinterpret_cast<const float4 *>(sd.s + i))
+                        : make_float4(i < N ? __ldcg(sd.s + i) : 0.0f, i + 1 < N ? __ldcg(sd.s + i + 1) : 0.0f,
+                                      i + 2 < N ? __ldcg(sd.s + i + 2) : 0.0f, 0.0f);
+    }
     uint64_t acc = 0;
 #pragma unroll
-    for (int q = 0; q < kSubTile / 128; ++q) {
+    for (int q = 0; q < kUnit / 128; ++q) {
       const int64_t i = i0 + q * 128 + lane * 4;
       const uint32_t e = __shfl_sync(kFullMask, evw, q * 4 + (lane >> 3)) >> ((lane & 7) * 4);
-      if (i + 3 < N) {
-        const float4 s4 = __ldcg(reinterpret_cast<const float4 *>(sd.s + i));
-        const float sa[4] = {s4.x, s4.y, s4.z, s4.w};
-        uint32_t w[4];
+      const float sa[4] = {sv[q].x, sv[q].y, sv[q].z, sv[q].w};
+      uint32_t w[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          w[c] = ((e >> c) & 1u) ? 0u : (uint32_t)weight_of(sa[c], smin, smax, gm);
-          acc += w[c];
-        }
+      for (int c = 0; c < 4; ++c) {
+        w[c] = (((e >> c) & 1u) || i + c >= N) ? 0u : (uint32_t)weight_of(sa[c], smin, smax, gm);
+        acc += w[c];
+      }
+      if (i + 3 < N) {
         __stcg(reinterpret_cast<uint4 *>(sd.w + i), make_uint4(w[0], w[1], w[2], w[3]));
       } else {
-        for (int c = 0; c < 4; ++c) {
-          if (i + c < N) {
-            const uint32_t w = ((e >> c) & 1u) ? 0u : (uint32_t)weight_of(__ldcg(sd.s + i + c), smin, smax, gm);
-            __stcg(sd.w + i + c, w);
-            acc += w;
-          }
-        }
+        for (int c = 0; c < 4; ++c)
+          if (i + c < N) __stcg(sd.w + i + c, w[c]);
       }
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFullMask, acc, o);
-    if (lane == 0) {
-      sd.sub_sum[gsub] = acc;
-      if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(sd.super_sum + gsub / kSuper),
-                         (unsigned long long)acc);
+    if (lane == 0 && acc) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(sd.sub_sum + i0 / kSubTile), (unsigned long long)acc);
+      if (super_here)
+        atomicAdd(reinterpret_cast<unsigned long long *>(sd.super_sum + i0 / (kSubTile * kSuper)),
+                  (unsigned long long)acc);
     }
   }
 }
@@ -259,11 +277,34 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   uint32_t *buf = reinterpret_cast<uint32_t *>(subc + kF3Sub);
   __shared__ int64_t spec_g[kSpec];
   const bool cached = n_sub <= kF3Sub;
-  for (int64_t i = threadIdx.x; i < n_super; i += THREADS) sup[i] = __ldcg(sd.super_sum + i);
-  if (cached)
-    for (int64_t i = threadIdx.x; i < n_sub; i += THREADS) subc[i] = __ldcg(sd.sub_sum + i);
+  // the tile sums, every copy in flight before one wait (pairs of sums per
+  // copy); with the sub-tile sums in shared memory the super-tile sums are
+  // their sums, else they were accumulated with the weights
+  if (cached) {
+    for (int64_t i = threadIdx.x; 2 * i < n_sub; i += THREADS) {
+      if (2 * i + 1 < n_sub) cp_async16(subc + 2 * i, sd.sub_sum + 2 * i);
+      else subc[2 * i] = __ldcg(sd.sub_sum + 2 * i);
+    }
+  } else {
+    for (int64_t i = threadIdx.x; 2 * i < n_super; i += THREADS) {
+      if (2 * i + 1 < n_super) cp_async16(sup + 2 * i, sd.super_sum + 2 * i);
+      else sup[2 * i] = __ldcg(sd.super_sum + 2 * i);
+    }
+  }
   if (threadIdx.x < kSpec) spec_g[threadIdx.x] = -1;
+  cp_async_wait_all();
   __syncthreads();
+  if (cached) {
+    for (int64_t sp = threadIdx.x; sp < n_super; sp += THREADS) {
+      uint64_t t = 0;
+      const int64_t g1 = min(n_sub, (sp + 1) * kSuper);
+      for (int64_t g = sp * kSuper; g < g1; ++g) t += subc[g];
+      sup[sp] = t;
+      sd.super_sum[sp] = t;      // for inspection; the draws use the shared copy
+    }
+    __syncthreads();
+  }
+
   const uint64_t seed = sd.seed;
   const uint32_t sid = sd.search_id, stp = st.step;
   const int64_t per = (n_super + 31) / 32;
@@ -317,24 +358,28 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
       if (locate(r, local, incl, sp, g, vg, r2)) {
         const int64_t i0 = g * kSubTile;
         uint32_t *b = buf + warp * kSubTile;
-        for (int q = lane; q < kSubTile / 4; q += 32) {
+        for (int q = lane; q < kSubTile / 4; q += 32) {   // all copies in flight at once
           const int64_t i = i0 + 4 * q;
-          uint4 x = make_uint4(0, 0, 0, 0);
-          if (i + 3 < N) x = __ldcg(reinterpret_cast<const uint4 *>(sd.w + i));
-          else {
+          if (i + 3 < N) {
+            cp_async16(b + 4 * q, sd.w + i);
+          } else {
+            uint4 x;
             x.x = i < N ? __ldcg(sd.w + i) : 0u;
             x.y = i + 1 < N ? __ldcg(sd.w + i + 1) : 0u;
             x.z = i + 2 < N ? __ldcg(sd.w + i + 2) : 0u;
+            x.w = 0u;
+            reinterpret_cast<uint4 *>(b)[q] = x;
           }
-          reinterpret_cast<uint4 *>(b)[q] = x;
         }
         if (lane == 0) spec_g[warp] = g;
       }
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   if (warp == 0) {
     uint32_t *__restrict__ wp = sd.w;
+    const int64_t my_spec = lane < kSpec ? spec_g[lane] : -1;   // the sub-tile fetched into buffer lane
     const uint64_t u_lo = philox_u64(seed, sid, stp, (uint32_t)lane, 0u);
     const uint64_t u_hi = lane + 32 < k ? philox_u64(seed, sid, stp, (uint32_t)(lane + 32), 0u) : 0ull;
     int count = 0;
@@ -348,12 +393,8 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
       uint64_t vg, r2;
       if (!locate(r, local, incl, sp, g, vg, r2)) break;   // cannot happen with consistent sums
       // the sub-tile's weights: a fetched copy, else from L2
-      int bsel = -1;
-      for (int b = 0; b < kSpec; ++b)
-        if (spec_g[b] == g) {
-          bsel = b;
-          break;
-        }
+      const unsigned has = __ballot_sync(kFullMask, my_spec == g);
+      const int bsel = has ? __ffs(has) - 1 : -1;
       const int64_t i0 = g * kSubTile + lane * 32;
       uint32_t wv[32];
       if (bsel >= 0) {
@@ -401,15 +442,19 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
         }
         acc += wv[q];
       }
-      if (mine && qsel >= 0) {
-        const int64_t i = i0 + qsel;
+      const unsigned got = __ballot_sync(kFullMask, mine && qsel >= 0);
+      if (!got) break;                 // cannot happen with consistent sums
+      const int src = __ffs(got) - 1;
+      const int64_t i = __shfl_sync(kFullMask, i0 + qsel, src);
+      const uint32_t wi = __shfl_sync(kFullMask, wsel, src);
+      // the pick's weight becomes 0 everywhere it is kept
+      if (my_spec == g) buf[lane * kSubTile + (i - g * kSubTile)] = 0u;
+      if (lane == 0) {
         pick[j] = i;
         wp[i] = 0;
-        for (int b = 0; b < kSpec; ++b)
-          if (spec_g[b] == g) buf[b * kSubTile + (i - g * kSubTile)] = 0u;
-        if (cached) subc[g] = vg - wsel;
-        else sd.sub_sum[g] = vg - wsel;
-        sup[sp] -= wsel;
+        if (cached) subc[g] = vg - wi;
+        else sd.sub_sum[g] = vg - wi;
+        sup[sp] -= wi;
         atomicOr(sd.eval + (i >> 5), 1u << (i & 31));
       }
       __syncwarp();
@@ -468,25 +513,15 @@ struct Scorer {
     }
   }
 
-  // the range [lo, hi): full chunks of CPT configurations per thread, then
-  // the remainder with fewer per thread
+  // the range [lo, hi) in the fewest chunks of at most THREADS x CPT
+  // configurations, all of (nearly) equal size, so that every chunk keeps
+  // CPT independent walks per thread
   template <int CPT>
   __device__ __forceinline__ void range(int64_t lo, int64_t hi) {
-    int64_t base = lo;
     constexpr int64_t full = (int64_t)THREADS * CPT;
-    for (; base + full <= hi; base += full) chunk<CPT>(base, hi);
-    if constexpr (CPT >= 4) {
-      constexpr int64_t half = (int64_t)THREADS * (CPT / 2);
-      if (base + half <= hi) {
-        chunk<CPT / 2>(base, hi);
-        base += half;
-      }
-    }
-    if constexpr (CPT >= 2) {
-      constexpr int64_t two = (int64_t)THREADS * 2;
-      for (; base + two <= hi; base += two) chunk<2>(base, hi);
-    }
-    for (; base < hi; base += THREADS) chunk<1>(base, hi);
+    const int64_t n_c = (hi - lo + full - 1) / full;
+    for (int64_t q = 0; q < n_c; ++q)
+      chunk<CPT>(lo + (hi - lo) * q / n_c, lo + (hi - lo) * (q + 1) / n_c);
   }
 };
 
@@ -508,13 +543,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   const int64_t N = sd.N;
   const int k = st.k;
 
+  const bool cta0 = blockIdx.x == 0;
+  stamp(fa, 0, cta0);
+  const int64_t lo = N * (int64_t)blockIdx.x / G, hi = N * (int64_t)(blockIdx.x + 1) / G;
+  // this CTA's digits and evaluated bits, brought into L2 while c_profile's walk runs
+  for (int64_t off = (int64_t)threadIdx.x * 32; off < hi - lo; off += (int64_t)THREADS * 32)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.narrow + lo + off));
+  for (int64_t off = (int64_t)threadIdx.x * 32; off < (hi - lo) / 32 + 1; off += (int64_t)THREADS * 32)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.eval + (lo >> 5) + off));
   // ---- P0: c_profile's prediction per counter, the active counters ----------------
+  // The node bytes of all K trees are copied into shared memory in one round
+  // trip when they fit, so that c_profile's walks do not wait on a chain of
+  // dependent global loads.
+  const bool staged = L >= 16 && (size_t)K * L <= (size_t)kFusedSmem;
+  if (staged) {
+    const int n16 = (K * L) >> 4;
+    for (int i = threadIdx.x; i < n16; i += THREADS)
+      cp_async16(smem + 16 * i, sd.nodes + 16 * (size_t)i);
+    cp_async_wait_all();
+    __syncthreads();
+  }
   if (warp == 0) {
     const uint32_t plo = (uint32_t)st.cprof_packed, phi = (uint32_t)(st.cprof_packed >> 32);
     for (int p = lane; p < K; p += 32) {
-      const uint8_t *nd = sd.nodes + (size_t)p * L;
+      const uint8_t *nd = staged ? smem + (size_t)p * L : sd.nodes + (size_t)p * L;
       uint32_t i = 0;
-      for (int l = 0; l < D; ++l) i = tree_step(i, __ldg(nd + i), plo, phi);
+      for (int l = 0; l < D; ++l) i = tree_step(i, staged ? nd[i] : __ldg(nd + i), plo, phi);
       sh_A[p] = __ldg(sd.leaves + (size_t)p * L + (i - (uint32_t)(L - 1)));
       sh_dl[p] = st.delta[p];
     }
@@ -543,8 +597,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     }
   }
 
+  stamp(fa, 1, cta0);
+  // ---- P0b: this CTA's share of the per-leaf summands of Eq. score -------------------
+  // summand of leaf i of active tree a: Delta_p (x - A) / (x + A) with x the
+  // leaf value and A = pc_p(c_profile), 0 when x or x + A is 0 (PC_used)
+  {
+    const int64_t total = (int64_t)n_active << D;
+    const int64_t per = (total + G - 1) / G;
+    const int64_t e_lo = min(total, per * blockIdx.x), e_hi = min(total, e_lo + per);
+    for (int64_t e = e_lo + threadIdx.x; e < e_hi; e += THREADS) {
+      const int p = sh_active[(int)(e >> D)];
+      const float A = sh_A[p], dl = sh_dl[p];
+      const float x = __ldg(sd.leaves + ((size_t)p << D) + (e & (L - 1)));
+      const float den = __fadd_rn(x, A);
+      float t = 0.0f;
+      if (x != 0.0f && den != 0.0f) t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(x, A), den));
+      fa.terms[e] = t;
+    }
+  }
+  if (!TOPK) {   // the sub-tile sums the weights add to, this CTA's slice
+    const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
+    const int64_t per = (n_sub + G - 1) / G;
+    const int64_t g0 = min(n_sub, per * blockIdx.x), g1 = min(n_sub, g0 + per);
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += THREADS) sd.sub_sum[g] = 0;
+  }
+  if (!grid_barrier(fa.sync, G, fa.wait_ns, &sh_ok) && threadIdx.x == 0)
+    atomicExch(fa.status, KTUNE_ETIMEOUT);
+  stamp(fa, 2, cta0);
   // ---- P1: score this CTA's range ------------------------------------------------
-  const int64_t lo = N * (int64_t)blockIdx.x / G, hi = N * (int64_t)(blockIdx.x + 1) / G;
   const int tree_words = 2 * L;
   const int budget = kFusedSmem - (TOPK ? kListBytes : 0);
   const int per_group = max(1, budget / (tree_words * 4));
@@ -559,29 +639,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     const int t0 = g * per_group;
     const int nt = max(0, min(per_group, n_active - t0));
     __syncthreads();   // the previous group's walks are done
-    // node words by asynchronous copies, then the summands from the leaf values
+    // node words and summands of the group's trees by asynchronous copies
     for (int a = 0; a < nt; ++a) {
       const int p = sh_active[t0 + a];
+      const uint32_t *wsrc = fa.words + (size_t)p * L;
+      const uint32_t *tsrc = reinterpret_cast<const uint32_t *>(fa.terms + (size_t)(t0 + a) * L);
+      uint32_t *dst = trees + (size_t)a * tree_words;
       if (L >= 4) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(fa.words + (size_t)p * L);
-        uint4 *dst = reinterpret_cast<uint4 *>(trees + (size_t)a * tree_words);
-        for (int i = threadIdx.x; i < L / 4; i += THREADS) cp_async16(dst + i, src + i);
+        for (int i = threadIdx.x; i < L / 2; i += THREADS) {
+          const bool w = i < L / 4;
+          const int q = w ? i : i - L / 4;
+          cp_async16(reinterpret_cast<uint4 *>(dst + (w ? 0 : L)) + q,
+                     reinterpret_cast<const uint4 *>(w ? wsrc : tsrc) + q);
+        }
       } else {
-        for (int i = threadIdx.x; i < L; i += THREADS)
-          trees[(size_t)a * tree_words + i] = __ldg(fa.words + (size_t)p * L + i);
-      }
-    }
-    for (int a = 0; a < nt; ++a) {
-      const int p = sh_active[t0 + a];
-      const float A = sh_A[p], dl = sh_dl[p];
-      const float *lv = sd.leaves + (size_t)p * L;
-      float *terms = reinterpret_cast<float *>(trees + (size_t)a * tree_words + L);
-      for (int i = threadIdx.x; i < L; i += THREADS) {
-        const float x = __ldg(lv + i);
-        const float den = __fadd_rn(x, A);
-        float t = 0.0f;
-        if (x != 0.0f && den != 0.0f) t = __fmul_rn(dl, __fdiv_rn(__fsub_rn(x, A), den));
-        terms[i] = t;
+        for (int i = threadIdx.x; i < 2 * L; i += THREADS)
+          dst[i] = i < L ? __ldg(wsrc + i) : __ldcg(tsrc + i - L);
       }
     }
     cp_async_wait_all();
@@ -624,8 +697,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     if (warp == 0) warp_merge(lists, NW, KTUNE_MAX_K, k, fa.cand + (size_t)blockIdx.x * KTUNE_MAX_K);
   } else {
     // ---- grid barrier: s_min and s_max are final ------------------------------------
+    stamp(fa, 3, cta0);
     if (!grid_barrier(fa.sync, G, fa.wait_ns, &sh_ok) && threadIdx.x == 0)
       atomicExch(fa.status, KTUNE_ETIMEOUT);
+    stamp(fa, 4, cta0);
     fused_weights(fa);
   }
 
@@ -637,8 +712,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     sh_last = ((old + 1) % G) == 0;
   }
   __syncthreads();
+  stamp(fa, 5, cta0);
   if (!sh_last) return;
   __threadfence();
+  stamp(fa, 6, true);
 
   __shared__ int64_t pick[KTUNE_MAX_K];
   __shared__ float pick_s[KTUNE_MAX_K];
@@ -681,6 +758,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     st.out_score[j] = pick_s[j];
     if (st.out_packed) st.out_packed[j] = p;
   }
+  stamp(fa, 7, true);
   if (threadIdx.x == 0) {
     if (st.n_out) *st.n_out = count;
     sd.mm[0] = __ldcg(fa.mm_live);
@@ -749,11 +827,12 @@ static const int kFusedShapes[][2] = {{512, 8}, {1024, 4}, {1024, 8}};
 
 int fused_shapes() { return (int)(sizeof(kFusedShapes) / sizeof(kFusedShapes[0])); }
 
+// CTAs of this shape resident per SM (the smaller of the sample and top-k forms).
 int fused_blocks_per_sm(int shape) {
   switch (shape) {
-    case 1: return blocks_per_sm_t<1024, 4, 0, false>();
-    case 2: return blocks_per_sm_t<1024, 8, 0, false>();
-    default: return blocks_per_sm_t<512, 8, 0, false>();
+    case 1: return std::min(blocks_per_sm_t<1024, 4, 0, false>(), blocks_per_sm_t<1024, 4, 0, true>());
+    case 2: return std::min(blocks_per_sm_t<1024, 8, 0, false>(), blocks_per_sm_t<1024, 8, 0, true>());
+    default: return std::min(blocks_per_sm_t<512, 8, 0, false>(), blocks_per_sm_t<512, 8, 0, true>());
   }
 }
 

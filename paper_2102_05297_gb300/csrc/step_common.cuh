@@ -131,10 +131,11 @@ __device__ __forceinline__ uint32_t narrow_word(uint32_t nb, const PrepArgs &pa)
 // child in the 1-based heap.  Trees are staged group by group; a CTA runs its
 // whole range through one group before staging the next, keeping the partial
 // score in s_out between groups (same float32 value, same summation order).
+// The child index is j + j + carry: one add with carry-in.
 __device__ __forceinline__ uint32_t narrow_visit(uint32_t j, uint32_t word, uint32_t W) {
   const uint32_t x = __funnelshift_l(0u, W, word);
   uint32_t sum;
-  asm("add.cc.u32 %0, %2, %3;\n\tmadc.lo.u32 %1, %1, 2, 0;" : "=r"(sum), "+r"(j) : "r"(x), "r"(word));
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, %1;" : "=r"(sum), "+r"(j) : "r"(x), "r"(word));
   return j;
 }
 
@@ -235,22 +236,17 @@ __device__ T block_incl(T v, T *sh, T *total) {
 // Eq. score_normalization in float32, each operation rounded, x^8 as
 // ((x^2)^2)^2, s = 0 mapped to 1; weight = round-half-even(s_norm * 2^20).
 __device__ __forceinline__ uint64_t weight_of(float s, float smin, float smax, float gamma) {
+  // both branches of the equation divide s by one extreme and take the 8th
+  // power of 1 +- the quotient: one division and one power serve either,
+  // without divergence; the result is selected afterwards
+  const bool pos = s > 0.0f;
+  const float q = __fdiv_rn(s, pos ? smax : smin);
+  const float x = pos ? __fadd_rn(1.0f, q) : __fsub_rn(1.0f, q);
+  const float x2 = __fmul_rn(x, x), x4 = __fmul_rn(x2, x2), x8 = __fmul_rn(x4, x4);
   float sn;
-  if (s > 0.0f) {
-    const float x = __fadd_rn(1.0f, __fdiv_rn(s, smax));
-    const float x2 = __fmul_rn(x, x), x4 = __fmul_rn(x2, x2);
-    sn = __fmul_rn(x4, x4);
-  } else if (s > gamma) {
-    if (s == 0.0f) {
-      sn = 1.0f;
-    } else {
-      const float y = __fsub_rn(1.0f, __fdiv_rn(s, smin));
-      const float y2 = __fmul_rn(y, y), y4 = __fmul_rn(y2, y2);
-      sn = fmaxf(1e-4f, __fmul_rn(y4, y4));
-    }
-  } else {
-    sn = 1e-4f;
-  }
+  if (pos) sn = x8;
+  else if (s > gamma) sn = s == 0.0f ? 1.0f : fmaxf(1e-4f, x8);
+  else sn = 1e-4f;
   // s_norm * 2^20 <= 2^28: the 32-bit conversion (round half even) is exact
   // and avoids the 64-bit one, which runs on the FP64 pipe
   return (uint64_t)__float2uint_rn(__fmul_rn(sn, 1048576.0f));
