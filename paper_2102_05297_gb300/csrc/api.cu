@@ -1238,7 +1238,7 @@ static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *
   if (h->last_fused) {
     // one cooperative launch: every CTA of the grid is resident at once
     FusedArgs fa{};
-    fa.srch = h->d_srch;
+    fa.sd = h->sdh;
     fa.words = h->d_fz_words;
     fa.terms = h->d_fz_terms;
     fa.mm_live = h->d_fz_mm;
@@ -1247,6 +1247,7 @@ static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *
     fa.cand = h->d_fz_cand;
     fa.wait_ns = 1000000000ull;
     fa.phase_ns = h->timing ? h->d_fz_phase : nullptr;
+    fa.four = 4;
     fa.st = sp;
     if (h->timing) CK(cudaEventRecord(h->ev[0], st));
     CK(launch_step_fused(fa, h->fused - 1, h->opts.select == KTUNE_SELECT_TOPK, h->model->D,

@@ -187,7 +187,7 @@ struct StepDev {
 // Launch parameters of the fused whole-step kernel (k_fused.cu): a tree
 // search over a materialised one-word space, the step by value.
 struct FusedArgs {
-  const SearchDev *srch;
+  SearchDev sd;                   // the search's descriptor, by value (read from the constant bank)
   const uint32_t *words;          // [K][L] node words of the one-word walk (word 0 of a tree unused)
   float *terms;                   // [K][L] the step's per-leaf summands, by active rank
   int *mm_live;                   // [2] ordered-int min / max accumulated during the step
@@ -196,6 +196,7 @@ struct FusedArgs {
   uint64_t *cand;                 // [grid][KTUNE_MAX_K] per-CTA top-k keys
   uint64_t wait_ns;               // limit of each barrier wait
   uint64_t *phase_ns;             // [8] phase time stamps (null: none taken)
+  uint32_t four;                  // 4, as a launch parameter (the walk's word-offset multiplier)
   StepDev st;
 };
 int fused_shapes();

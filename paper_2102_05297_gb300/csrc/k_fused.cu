@@ -45,7 +45,7 @@ extern __shared__ __align__(16) uint8_t fz_smem[];
 constexpr int kSpec = 16;                // draws whose sub-tile is fetched ahead
 constexpr int kF3Super = kMaxSuper;      // P3: super-tile sums in shared memory
 constexpr int kF3Sub = 4096;             // P3: sub-tile sums kept in shared memory when they fit
-static_assert(kF3Super * 8 + kF3Sub * 8 + kSpec * kSubTile * 4 <= kFusedSmem, "P3 layout");
+static_assert(kF3Super * 8 + kF3Sub * 8 + (kSpec + 1) * kSubTile * 4 <= kFusedSmem, "P3 layout");
 
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
@@ -165,15 +165,27 @@ __device__ void warp_merge(const uint64_t *lists, int n, int stride, int k, uint
 // add the summand of the leaf reached in each; a staged tree is 2L words:
 // node words at 1 .. L-1 (1-based heap) and the leaf summands at L .. 2L-1,
 // so the index the walk ends on addresses its summand directly.
+// Word j of the tree at shared address tb.  The byte offset is j times a
+// run-time 4 (a launch parameter): an index scaled by a value the compiler
+// cannot see is computed with a multiply-add, which runs on the multiply
+// pipe, and leaves the integer pipe -- the walk's bound -- to the shift and
+// the adds of the visit.
+__device__ __forceinline__ uint32_t tree_word(uint32_t tb, uint32_t j, uint32_t four) {
+  uint32_t a, w;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(a) : "r"(j), "r"(four), "r"(tb));
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(a));
+  return w;
+}
+
 template <int DT, int CPT>
-__device__ __forceinline__ void walk_trees(int nt, int D, int L, const uint32_t (&W)[CPT],
+__device__ __forceinline__ void walk_trees(int nt, int D, int L, uint32_t four, const uint32_t (&W)[CPT],
                                            float (&s)[CPT]) {
-  const uint32_t *trees = reinterpret_cast<const uint32_t *>(fz_smem);
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(fz_smem);
   for (int a = 0; a < nt; ++a) {
-    const uint32_t *t = trees + a * 2 * L;
+    const uint32_t tb = base + (uint32_t)(a * 8 * L);
     // the root is the same node for every configuration: one load, then the
     // remaining levels
-    const uint32_t root = t[1];
+    const uint32_t root = tree_word(tb, 1u, four);
     uint32_t j[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(1u, root, W[c]);
@@ -181,16 +193,16 @@ __device__ __forceinline__ void walk_trees(int nt, int D, int L, const uint32_t 
 #pragma unroll
       for (int l = 1; l < DT; ++l) {
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], t[j[c]], W[c]);
+        for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], tree_word(tb, j[c], four), W[c]);
       }
     } else {
       for (int l = 1; l < D; ++l) {
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], t[j[c]], W[c]);
+        for (int c = 0; c < CPT; ++c) j[c] = narrow_visit(j[c], tree_word(tb, j[c], four), W[c]);
       }
     }
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) s[c] = __fadd_rn(s[c], __uint_as_float(t[j[c]]));
+    for (int c = 0; c < CPT; ++c) s[c] = __fadd_rn(s[c], __uint_as_float(tree_word(tb, j[c], four)));
   }
 }
 
@@ -201,7 +213,7 @@ __device__ __forceinline__ void walk_trees(int nt, int D, int L, const uint32_t 
 // when the draws cannot sum the sub-tiles in shared memory themselves.
 // Out of line, so that its registers do not count against the walk's.
 __device__ __noinline__ void fused_weights(const FusedArgs &fa) {
-  const SearchDev &sd = *fa.srch;
+  const SearchDev &sd = fa.sd;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
   const int64_t N = sd.N;
   const float smin = okey_inv(__ldcg(fa.mm_live)), smax = okey_inv(__ldcg(fa.mm_live + 1));
@@ -257,7 +269,7 @@ __device__ __noinline__ void fused_weights(const FusedArgs &fa) {
 // than k once every remaining weight is 0) with their ordinals in pick[].
 // Out of line, so that its registers do not count against the walk's.
 __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
-  const SearchDev &sd = *fa.srch;
+  const SearchDev &sd = fa.sd;
   const StepDev &st = fa.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int THREADS = blockDim.x;
@@ -383,70 +395,66 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
     const uint64_t u_lo = philox_u64(seed, sid, stp, (uint32_t)lane, 0u);
     const uint64_t u_hi = lane + 32 < k ? philox_u64(seed, sid, stp, (uint32_t)(lane + 32), 0u) : 0ull;
     int count = 0;
+    // the super-tile totals once; each pick then lowers them where it lies
+    uint64_t local, incl;
+    uint64_t W = totals(local, incl);
     for (int j = 0; j < k; ++j) {
-      uint64_t local, incl;
-      const uint64_t W = totals(local, incl);
       if (W == 0) break;
       const uint64_t uj = j < 32 ? __shfl_sync(kFullMask, u_lo, j) : __shfl_sync(kFullMask, u_hi, j - 32);
       const uint64_t r = scaled_draw(uj, W);
       int64_t sp, g;
       uint64_t vg, r2;
       if (!locate(r, local, incl, sp, g, vg, r2)) break;   // cannot happen with consistent sums
-      // the sub-tile's weights: a fetched copy, else from L2
+      // the sub-tile's weights in shared memory: a fetched copy, else copied
+      // now into the scratch buffer kSpec (earlier draws zeroed theirs in L2)
       const unsigned has = __ballot_sync(kFullMask, my_spec == g);
-      const int bsel = has ? __ffs(has) - 1 : -1;
-      const int64_t i0 = g * kSubTile + lane * 32;
-      uint32_t wv[32];
-      if (bsel >= 0) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(buf + bsel * kSubTile + lane * 32);
+      int bsel = has ? __ffs(has) - 1 : kSpec;
+      if (bsel == kSpec) {
+        uint32_t *b = buf + kSpec * kSubTile;
+        for (int q = lane; q < kSubTile / 4; q += 32) {
+          const int64_t i = g * kSubTile + 4 * q;
+          if (i + 3 < N) {
+            cp_async16(b + 4 * q, wp + i);
+          } else {
+            uint4 x;
+            x.x = i < N ? __ldcg(wp + i) : 0u;
+            x.y = i + 1 < N ? __ldcg(wp + i + 1) : 0u;
+            x.z = i + 2 < N ? __ldcg(wp + i + 2) : 0u;
+            x.w = 0u;
+            reinterpret_cast<uint4 *>(b)[q] = x;
+          }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        // the earlier picks in this sub-tile read 0 whatever the copy saw
+        for (int q = lane; q < count; q += 32)
+          if (pick[q] / kSubTile == g) b[pick[q] - g * kSubTile] = 0u;
+        __syncwarp();
+      }
+      const uint32_t *bw = buf + bsel * kSubTile;
+      // lane l: the sum of weights 32 l .. 32 l + 31, then a scan over the lanes
+      uint64_t ls = 0;
+      {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(bw + lane * 32);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const uint4 x = s4[q];
-          wv[4 * q] = x.x;
-          wv[4 * q + 1] = x.y;
-          wv[4 * q + 2] = x.z;
-          wv[4 * q + 3] = x.w;
+          ls += (uint64_t)x.x + x.y + (uint64_t)x.z + x.w;
         }
-      } else if (i0 + 31 < N) {
-        const uint4 *w4 = reinterpret_cast<const uint4 *>(wp + i0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint4 x = __ldcg(w4 + q);
-          wv[4 * q] = x.x;
-          wv[4 * q + 1] = x.y;
-          wv[4 * q + 2] = x.z;
-          wv[4 * q + 3] = x.w;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) wv[q] = i0 + q < N ? __ldcg(wp + i0 + q) : 0u;
       }
-      uint64_t t16[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) t16[q] = (uint64_t)wv[2 * q] + wv[2 * q + 1];
-#pragma unroll
-      for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-        for (int q = 0; q < w; ++q) t16[q] = t16[2 * q] + t16[2 * q + 1];
-      const uint64_t ls = t16[0];
       const uint64_t inc3 = warp_incl(ls);
-      const bool mine = inc3 - ls <= r2 && r2 < inc3;
-      uint64_t acc = inc3 - ls;
-      int qsel = -1;
-      uint32_t wsel = 0;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        if (mine && qsel < 0 && r2 < acc + wv[q]) {
-          qsel = q;
-          wsel = wv[q];
-        }
-        acc += wv[q];
-      }
-      const unsigned got = __ballot_sync(kFullMask, mine && qsel >= 0);
-      if (!got) break;                 // cannot happen with consistent sums
-      const int src = __ffs(got) - 1;
-      const int64_t i = __shfl_sync(kFullMask, i0 + qsel, src);
-      const uint32_t wi = __shfl_sync(kFullMask, wsel, src);
+      const unsigned own = __ballot_sync(kFullMask, inc3 - ls <= r2 && r2 < inc3);
+      if (!own) break;                 // cannot happen with consistent sums
+      // the lane holding r2; its 32 weights, one per lane, scanned by the warp
+      const int ol = __ffs(own) - 1;
+      const uint64_t rr = r2 - __shfl_sync(kFullMask, inc3 - ls, ol);
+      const uint32_t wq = bw[ol * 32 + lane];
+      const uint64_t iq = warp_incl((uint64_t)wq);
+      const unsigned hit = __ballot_sync(kFullMask, iq - wq <= rr && rr < iq);
+      if (!hit) break;
+      const int qs = __ffs(hit) - 1;
+      const int64_t i = g * kSubTile + ol * 32 + qs;
+      const uint32_t wi = __shfl_sync(kFullMask, wq, qs);
       // the pick's weight becomes 0 everywhere it is kept
       if (my_spec == g) buf[lane * kSubTile + (i - g * kSubTile)] = 0u;
       if (lane == 0) {
@@ -456,6 +464,12 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
         else sd.sub_sum[g] = vg - wi;
         sup[sp] -= wi;
         atomicOr(sd.eval + (i >> 5), 1u << (i & 31));
+      }
+      {
+        const int o = (int)(sp / per);   // the lane whose super-tile slice holds sp
+        if (lane == o) local -= wi;
+        if (lane >= o) incl -= wi;
+        W -= wi;
       }
       __syncwarp();
       ++count;
@@ -471,6 +485,7 @@ struct Scorer {
   static constexpr int NW = THREADS / 32;
   const SearchDev &sd;
   int nt, D, L, k;
+  uint32_t four;
   bool first, last;
   float mn, mx;
   bool any;
@@ -494,7 +509,7 @@ struct Scorer {
       s[c] = (first || !ok[c]) ? 0.0f : __ldcg(s_p + i);
       ev[c] = (last && ok[c]) ? (__ldg(eval_p + (i >> 5)) >> (i & 31)) & 1u : 0u;
     }
-    walk_trees<DT, CPT>(nt, D, L, W, s);
+    walk_trees<DT, CPT>(nt, D, L, four, W, s);
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       const int64_t i = base + (int64_t)c * THREADS + threadIdx.x;
@@ -535,7 +550,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   __shared__ int sh_nact, sh_ok, sh_last;
   __shared__ float red_mn[NW], red_mx[NW];
   __shared__ int sh_any[NW];
-  const SearchDev &sd = *fa.srch;
+  const SearchDev &sd = fa.sd;
   const StepDev &st = fa.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned G = gridDim.x;
@@ -631,7 +646,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   const int n_groups = max(1, (n_active + per_group - 1) / per_group);
   uint32_t *trees = reinterpret_cast<uint32_t *>(smem);
   uint64_t *lists = reinterpret_cast<uint64_t *>(smem + kFusedSmem - kListBytes);
-  Scorer<THREADS, DT, TOPK> sc{sd, 0, D, L, k, true, false, FLT_MAX, -FLT_MAX, false,
+  Scorer<THREADS, DT, TOPK> sc{sd, 0, D, L, k, fa.four, true, false, FLT_MAX, -FLT_MAX, false,
                                lists + warp * KTUNE_MAX_K};
   if (TOPK)
     for (int e = lane; e < KTUNE_MAX_K; e += 32) sc.tk[e] = 0ull;
@@ -744,14 +759,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     const int count = fused_draws(fa, pick);
     if (threadIdx.x == 0) sh_count = count;
     __syncthreads();
-    if ((int)threadIdx.x < count) pick_s[threadIdx.x] = __ldcg(sd.s + pick[threadIdx.x]);
-    __syncthreads();
   }
   // outputs; the step's min / max for the statistics; the accumulator reset
   const int count = sh_count;
   if ((int)threadIdx.x < count) {
     const int j = threadIdx.x;
     const uint64_t p = __ldg(sd.packed + pick[j]);
+    if (!TOPK) pick_s[j] = __ldcg(sd.s + pick[j]);
     int64_t raw = 0;
     for (int q = 0; q < sd.sa.P; ++q) raw += (int64_t)nib64(p, q) * sd.sa.stride[q];
     st.out_raw[j] = raw;
