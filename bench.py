@@ -68,7 +68,7 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
-ALL_PATHS = ("chain", "mlp", "lsq", "cached", "nbr", "batch", "large", "tiny")
+ALL_PATHS = ("chain", "mlp", "lsq", "cached", "table", "nbr", "batch", "large", "tiny")
 # DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
 # captures summarised under profiles/ (the kernels have not changed since)
 PROFILED_TRAFFIC = {
@@ -339,6 +339,9 @@ def run_ours(args):
             paths["chain"] = path_chain(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "cached" in want:
             paths["cached"] = path_cached(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
+        if "table" in want:
+            paths["table"] = path_table(ctx, wl, roles, gpu, sp, digits, traj,
+                                        fused_ms=1e3 * t_total / K)
         if "nbr" in want:
             paths["nbr"] = path_nbr(ctx, wl, sp, m, traj, fused_ms=1e3 * t_total / K)
         if "batch" in want:
@@ -728,6 +731,54 @@ def path_cached(ctx, wl, sp, m, traj, fused_ms):
     }
 
 
+def path_table(ctx, wl, roles, gpu, sp, digits, traj, fused_ms):
+    """The headline search with the measured counters of every configuration
+    as the model (model blob kind 2; the exact-counter experiment of Section
+    4): each step streams the active counters' columns of the table."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    Wu, n_steps = ctx["warmup"], ctx["steps"]
+    k = wl["k"]
+    table = np.ascontiguousarray(gpu.evaluate(digits)[0], np.float32)
+    t0 = time.perf_counter()
+    m = kt.Model(sp, {"kind": "table", "roles": roles, "table": table})
+    load_ms = 1e3 * (time.perf_counter() - t0)
+    bufs = (torch.empty(k, dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(k, dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+    s = kt.Search(sp, m, k=k, seed=0, stream=stream)
+    untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+    step_ms, _, _, scored, _ = timed_device_steps(kt, torch, s, traj, Wu, Wu + n_steps, k, stream,
+                                                  flush)
+    s.close()
+    s = kt.Search(sp, m, k=k, seed=0, stream=stream)
+    s.set_timing(True)
+    untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+    _, kern_ms, _, _, nact = timed_device_steps(kt, torch, s, traj, Wu, Wu + n_steps, k, stream, flush)
+    s.close()
+    m.close()
+    t = sum(step_ms) / 1e3
+    ns = len(step_ms)
+    # algorithmic bytes per scored configuration: 4 per active counter's
+    # column entry, 4 per score written, 1/8 per evaluated bit
+    bytes_ = sum(float(scored) / ns * (4.0 * a + 4.125) for a in nact)
+    ach = bytes_ / (kern_ms[1] / 1e3)
+    peak = float(ctx["pk"].get("hbm_gbs", 6800.0)) * 1e9
+    tot = kern_ms[:4].sum()
+    return {
+        "workload": "the headline search over a table of the measured (noise-free synthetic) "
+                    "counters of all %d configurations as the model" % (scored // ns),
+        "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / ns,
+        "steps_per_s": ns / t, "steps": ns, "load_ms": load_ms,
+        "speedup_vs_fused_trees": fused_ms / (1e3 * t / ns),
+        "roofline": {"bound": "hbm", "kernel": "k_cscore (Eq. score from the table's columns)",
+                     "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "peak_source": "%s STREAM-style copy" % ctx["src"],
+                     "bytes_per_config": "4 x active counters (mean %.2f) + 4.125" % np.mean(nact),
+                     "kernel_share": {"prepare": kern_ms[0] / tot, "score": kern_ms[1] / tot,
+                                      "weights": kern_ms[2] / tot, "select": kern_ms[3] / tot}},
+    }
+
+
 BATCH_SPACES = ["batch_%d" % i for i in range(8)]
 BATCH_K = [16, 32, 40, 32, 16, 40, 32, 16]
 
@@ -973,6 +1024,53 @@ def oracle_step_time(wl, roles, model, dig, counters, seed=0, step=0):
     return time.perf_counter() - t0, int(free.sum())
 
 
+# ---- the oracle on every host core: worker state and tasks (spawned processes) ----
+_W = {}
+
+
+def _oracle_init(model, dig, prof, d32):
+    _W.update(model=model, dig=dig, prof=prof, d32=d32)
+
+
+def _oracle_scores(lohi):
+    from oracle import score as oscore, trees as otrees
+    lo, hi = lohi
+    return oscore.score_fp32(_W["prof"], otrees.predict(_W["model"], _W["dig"][lo:hi]), _W["d32"])
+
+
+def _oracle_weights(args):
+    from oracle import select as oselect
+    s, smin, smax = args
+    return oselect.quantise(oselect.normalise_fp32(s, smin, smax))
+
+
+def oracle_step_time_allcores(wl, roles, model, dig, counters, n_proc):
+    """The oracle step of oracle_step_time with its per-configuration work
+    (predictions, Eq. score, normalisation and weights) split over n_proc
+    spawned processes; the draws run in the parent.  Pool start-up and the
+    workers' copies of the inputs are outside the timed region."""
+    import multiprocessing as mp
+    from oracle import expert, select as oselect, trees as otrees
+    prof = otrees.predict(model, dig[:1])[0]
+    d32 = expert.delta_vector(roles, counters).astype(np.float32)
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    edges = np.linspace(1, len(dig), n_proc + 1).astype(np.int64)   # configuration 0 is c_profile
+    parts = [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:])]
+    with mp.get_context("spawn").Pool(n_proc, initializer=_oracle_init,
+                                      initargs=(model, dig, prof, d32)) as pool:
+        pool.map(_oracle_scores, [(0, 1)] * n_proc)           # every worker started and warm
+        t0 = time.perf_counter()
+        sc = pool.map(_oracle_scores, parts)
+        smin = min(float(x.min()) for x in sc)
+        smax = max(float(x.max()) for x in sc)
+        ws = pool.map(_oracle_weights, [(x, np.float32(smin), np.float32(smax)) for x in sc])
+        w = np.concatenate([np.zeros(1, np.uint64)] + ws)
+        oselect.weighted_draws(w, wl["k"], 0, 0, 0)
+        t = time.perf_counter() - t0
+    return t, len(dig) - 1
+
+
 def cpu_baseline(name, model, counters, n_sample=None):
     wl = WORKLOADS[name]
     desc = load_desc(wl)
@@ -980,11 +1078,19 @@ def cpu_baseline(name, model, counters, n_sample=None):
     n_sample = n_sample or (1_000_000 if desc.n_raw > 1e7 else min(desc.n_raw, 1_000_000))
     raw, dig = oracle_sample(desc, n_sample)
     t, n = oracle_step_time(wl, roles, model, dig, counters)
-    return {"value": n / t, "unit": "configs/s", "cores": 1, "kind": "oracle",
-            "host_cores": os.cpu_count(),
-            "sample": "one oracle step (numpy, single thread) over %d valid configurations drawn "
-                      "uniformly from the workload's space, same model and counters" % len(raw),
-            "seconds": t}
+    out = {"value": n / t, "unit": "configs/s", "cores": 1, "kind": "oracle",
+           "host_cores": os.cpu_count(),
+           "sample": "one oracle step (numpy, single thread) over %d valid configurations drawn "
+                     "uniformly from the workload's space, same model and counters" % len(raw),
+           "seconds": t}
+    n_proc = os.cpu_count() or 1
+    if n_proc > 1:
+        ta, na = oracle_step_time_allcores(wl, roles, model, dig, counters, n_proc)
+        out["all_cores"] = {"value": na / ta, "unit": "configs/s", "cores": n_proc, "kind": "oracle",
+                            "sample": "the same step over the same sample, its per-configuration "
+                                      "work split over %d spawned processes (one per host core)"
+                                      % n_proc, "seconds": ta}
+    return out
 
 
 def run_reference(args):

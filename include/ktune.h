@@ -159,7 +159,8 @@ const uint64_t *ktune_space_packed_device(const ktune_space *space);
 /* ---- model (Section 3.3) ----------------------------------------------------
  * Parses a model blob (little-endian):
  *   uint32 magic 0x314D544B ("KTM1"), uint32 version 1, uint32 kind (1 = tree
- *   ensemble, 3 = least squares), uint32 K (1..KTUNE_MAX_COUNTERS), int32 roles[K];
+ *   ensemble, 2 = measured counter table, 3 = least squares), uint32 K
+ *   (1..KTUNE_MAX_COUNTERS), int32 roles[K];
  *   kind 1 (Section 3.3.2): then per counter: uint32 n_nodes, int32 feature[n]
  *   (-1 = leaf), int32 threshold[n] (right iff digit > threshold), int32
  *   left[n], int32 right[n], float value[n] (leaf values, finite); node 0 is
@@ -175,6 +176,14 @@ const uint64_t *ktune_space_packed_device(const ktune_space *space);
  *   prediction is the float32 multiply-add chain over the terms in that
  *   order.  Depth is reported as 0.  Searches need a materialised space and
  *   KTUNE_SELECT_SAMPLE, and are not accepted by ktune_batch_create.
+ *   kind 2 (the exact-counter experiment of Section 4, Table "tab:pc_bias": the
+ *   counters measured for every configuration stand in for a model): then
+ *   uint64 N (the space's valid count) and float counters[N][K] in TS order
+ *   (finite).  Needs a materialised space (KTUNE_ESTATE otherwise).  A step
+ *   takes c_profile's row as its prediction and computes Eq. score from the
+ *   table's columns (stored one column per counter, the layout of cached
+ *   predictions); searches need KTUNE_SELECT_SAMPLE, are not accepted by
+ *   ktune_batch_create, and refuse ktune_search_set_cached.  Depth is 0.
  * Malformed blobs or a shape that does not match the space give KTUNE_EMODEL.
  * The model is copied to the device; it keeps a pointer to the space, which
  * must outlive it. */

@@ -618,6 +618,50 @@ const uint64_t *ktune_space_packed_device(const ktune_space *s) { return s ? s->
 // three or more values are the m regressors (T = 1 + 2m + m(m-1)/2), each
 // regressor's value v mapped to u = 2 (log2(1 + v) - lo) / (hi - lo) - 1 over
 // its value list (float64 here, stored as float32).
+// Model blob kind 2: the measured counters of every configuration of TS (the
+// exact-counter experiment of Section 4, Table "tab:pc_bias": a table in place
+// of a fitted model), uint64 N then float32 [N][K] in TS order.  Stored as
+// one column per counter (the cached-prediction layout).
+static int load_table(ktune_space *s, const uint8_t *b, size_t bytes, int K, const std::vector<int> &roles,
+                      ktune_model **out) {
+  if (!s->d_packed) FAIL(KTUNE_ESTATE, "a counter table needs a materialised space");
+  uint64_t n = 0;
+  if (bytes < 8) FAIL(KTUNE_EMODEL, "blob truncated");
+  memcpy(&n, b, 8);
+  if ((int64_t)n != s->n_valid) FAIL(KTUNE_EMODEL, "the table's row count differs from the space's TS");
+  if (bytes != 8 + n * (size_t)K * 4) FAIL(KTUNE_EMODEL, "table size does not match N x K");
+  const float *rows = reinterpret_cast<const float *>(b + 8);
+  const int64_t Np = (s->n_valid + 7) / 8 * 8;
+  std::vector<float> cols((size_t)K * Np, 0.0f);
+  for (int64_t i = 0; i < s->n_valid; ++i)
+    for (int c = 0; c < K; ++c) {
+      float v;
+      memcpy(&v, rows + (size_t)i * K + c, 4);
+      if (!isfinite(v)) FAIL(KTUNE_EMODEL, "non-finite counter in the table");
+      cols[(size_t)c * Np + i] = v;
+    }
+  ktune_model *m = new (std::nothrow) ktune_model();
+  if (!m) FAIL(KTUNE_ENOMEM, "host allocation");
+  m->space = s;
+  m->K = K;
+  m->D = 0;
+  m->kind = 4;
+  m->roles = roles;
+  m->table_np = Np;
+  int rc;
+  if ((rc = dalloc(&m->d_table, cols.size()))) {
+    delete m;
+    return rc;
+  }
+  if (cudaMemcpy(m->d_table, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->d_table);
+    delete m;
+    FAIL(KTUNE_ECUDA, "table upload failed");
+  }
+  *out = m;
+  return KTUNE_OK;
+}
+
 static int load_lsq(ktune_space *s, const uint8_t *b, size_t bytes, int K, const std::vector<int> &roles,
                     ktune_model **out) {
   LsqDev q{};
@@ -699,7 +743,7 @@ int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model
   uint32_t magic, ver, kind, K;
   if (!rd32(&magic) || !rd32(&ver) || !rd32(&kind) || !rd32(&K)) FAIL(KTUNE_EMODEL, "blob truncated");
   if (magic != 0x314D544Bu || ver != 1) FAIL(KTUNE_EMODEL, "bad magic or version");
-  if (kind != 1 && kind != 3) FAIL(KTUNE_EMODEL, "unsupported model kind");
+  if (kind != 1 && kind != 2 && kind != 3) FAIL(KTUNE_EMODEL, "unsupported model kind");
   if (K < 1 || K > KTUNE_MAX_COUNTERS) FAIL(KTUNE_EMODEL, "K out of range");
   std::vector<int> roles(K);
   for (uint32_t k = 0; k < K; ++k) {
@@ -709,6 +753,7 @@ int ktune_model_load(ktune_space *s, const void *blob, size_t bytes, ktune_model
     roles[k] = (int)r;
   }
   if (kind == 3) return load_lsq(s, b + pos, bytes - pos, (int)K, roles, out);
+  if (kind == 2) return load_table(s, b + pos, bytes - pos, (int)K, roles, out);
   struct Tree {
     std::vector<int32_t> f, t, l, r;
     std::vector<float> v;
@@ -810,6 +855,7 @@ int ktune_model_destroy(ktune_model *m) {
   }
   cudaFree(m->d_nodes);
   cudaFree(m->d_leaves);
+  cudaFree(m->d_table);
   cudaFree(m->d_lsq);
   cudaFree(m->d_lsq_utab);
   cudaFree(m->d_lsq_coef);
@@ -831,6 +877,11 @@ int ktune_model_predict_device(const ktune_model *m, int64_t first, int64_t coun
   if (!s->d_packed) FAIL(KTUNE_ESTATE, "space is not materialised");
   if (first < 0 || count < 0 || first + count > s->n_valid) FAIL(KTUNE_EINVAL, "range out of TS");
   if (m->kind == 2) return ktune_mlp_predict_device(m->mlp, first, count, out, stream);
+  if (m->kind == 4) {
+    launch_cols_to_rows(m->d_table, m->table_np, m->K, first, count, out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return KTUNE_OK;
+  }
   if (m->kind == 3) {
     launch_lsq_predict(m->d_lsq, s->d_packed + first, count, out, (cudaStream_t)stream);
     CK(cudaGetLastError());
@@ -856,6 +907,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   if (s->n_valid == 0) FAIL(KTUNE_EXHAUSTED, "empty tuning space");
   if (m->kind == 2 && (!s->d_packed || o->select != KTUNE_SELECT_SAMPLE))
     FAIL(KTUNE_ESTATE, "MLP models need a materialised space and KTUNE_SELECT_SAMPLE");
+  if (m->kind == 4 && o->select != KTUNE_SELECT_SAMPLE)
+    FAIL(KTUNE_ESTATE, "counter-table models need KTUNE_SELECT_SAMPLE");
   if (m->kind == 3 && (!s->d_packed || o->select != KTUNE_SELECT_SAMPLE))
     FAIL(KTUNE_ESTATE, "least-squares models need a materialised space and KTUNE_SELECT_SAMPLE");
   const bool otf = s->flags == KTUNE_ON_THE_FLY;
@@ -1121,7 +1174,13 @@ static void launch_step_kernels(ktune_search *h, const StepBatch<1> &sb, cudaStr
     mark(4);
     return;
   }
-  if (h->cached) {
+  if (m->kind == 4) {
+    // a measured counter table: the step's set-up with c_profile's row, then
+    // Eq. score from the table's columns of the active counters
+    launch_table_prep(h->d_srch, h->d_steps, sb, m->d_table, m->table_np, st);
+    mark(1);
+    launch_cscore(h->d_srch, m->d_table, m->table_np, h->num_sms, st);
+  } else if (h->cached) {
     // cached predictions: the step's set-up and c_profile prediction, then
     // Eq. score from the cached columns of the active counters
     if (m->kind == 2) {
@@ -1190,7 +1249,7 @@ static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st)
       cudaKernelNodeParams kp{};
       CK(cudaGraphKernelNodeGetParams(nd, &kp));
       if (kp.func == bprep_func<1>() || kp.func == mlp_prep_func() || kp.func == lsq_prep_func() ||
-          kp.func == nbr_score_func())
+          kp.func == nbr_score_func() || kp.func == table_prep_func())
         h->prep_node = nd;
     }
     if (!h->prep_node) FAIL(KTUNE_ECUDA, "graph capture lost the prepare kernel");
@@ -1200,7 +1259,9 @@ static int launch_step_graph(ktune_search *h, StepBatch<1> &sb, cudaStream_t st)
   } else {
     cudaKernelNodeParams kp{};
     CK(cudaGraphKernelNodeGetParams(h->prep_node, &kp));
-    void *args[] = {&h->d_srch, &h->d_steps, &sb};
+    float *table = h->model->d_table;
+    int64_t table_np = h->model->table_np;
+    void *args[] = {&h->d_srch, &h->d_steps, &sb, &table, &table_np};
     kp.kernelParams = args;
     kp.extra = nullptr;
     CK(cudaGraphExecKernelNodeSetParams(h->gexec, h->prep_node, &kp));
@@ -1513,6 +1574,8 @@ static int set_lsq_pack(ktune_search *h, bool on) {
 
 int ktune_search_set_cached(ktune_search *h, int enable) {
   if (!h) FAIL(KTUNE_EINVAL, "null search");
+  if (enable && h->model->kind == 4)
+    FAIL(KTUNE_ESTATE, "a counter-table model is scored from its table already");
   if (!enable) {
     if (h->cached || h->d_cache || h->d_leaf_cache) {
       CK(cudaStreamSynchronize(h->last_stream ? h->last_stream : h->stream));
@@ -1823,6 +1886,7 @@ int ktune_batch_create(ktune_search *const *searches, int n, void *stream, ktune
       FAIL(KTUNE_EINVAL, "searches of a batch must share the select mode");
     if (searches[i]->model->kind == 1 && tree0 < 0) tree0 = i;
     if (searches[i]->model->kind == 3) FAIL(KTUNE_EINVAL, "least-squares searches step on their own");
+    if (searches[i]->model->kind == 4) FAIL(KTUNE_EINVAL, "counter-table searches step on their own");
     if (searches[i]->nbr_radius) FAIL(KTUNE_EINVAL, "neighbourhood-restricted searches step on their own");
   }
   for (int i = 0; i < n; ++i)

@@ -146,7 +146,7 @@ struct SearchDev {
   uint32_t ci_stride[KTUNE_MAX_PARAMS];
   const uint8_t *nodes;
   const float *leaves;
-  int kind;                   // model kind: 1 trees, 2 MLP, 3 least squares (own kernels)
+  int kind;                   // model kind: 1 trees, 2 MLP, 3 least squares, 4 counter table (own kernels)
   const LsqDev *lsq;          // kind 3: the model on the device
   int lsq_pack;               // kind 3: the prepare kernel writes the score kernel's pack (fused steps)
   const NbrDev *nbr;          // neighbourhood-restricted steps (null: the whole space)
@@ -326,6 +326,13 @@ void launch_leaf_cols(const uint64_t *packed, int64_t N, const uint8_t *nodes, i
 void launch_cscore_leaf(const SearchDev *srch, const uint16_t *leaves, int64_t Np, int tree_bytes,
                         int terms_off, int num_sms, cudaStream_t st);
 
+// measured counter tables (model blob kind 2; k_cache.cu)
+void launch_table_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,
+                       const float *table, int64_t Np, cudaStream_t st);
+const void *table_prep_func();
+void launch_cols_to_rows(const float *cols, int64_t Np, int K, int64_t first, int64_t count,
+                         float *out, cudaStream_t st);
+
 // least-squares counter model (k_lsq.cu)
 void launch_lsq_predict(const LsqDev *q, const uint64_t *packed, int64_t n, float *out, cudaStream_t st);
 // bytes of a search's buffer for the step's coefficient pack (all K counters active)
@@ -425,7 +432,9 @@ struct ktune_model {
   ktune_space *space = nullptr;
   int K = 0;
   int D = 0;
-  int kind = 1;                 // 1 trees, 2 MLP (not owned), 3 least squares
+  int kind = 1;                 // 1 trees, 2 MLP (not owned), 3 least squares, 4 counter table
+  float *d_table = nullptr;     // kind 4: [K][table_np] measured counters, one column per counter
+  int64_t table_np = 0;
   ktune_mlp *mlp = nullptr;
   ktune::LsqDev *d_lsq = nullptr;   // kind 3: descriptor, u table and coefficients
   float *d_lsq_utab = nullptr, *d_lsq_coef = nullptr;

@@ -301,6 +301,65 @@ __global__ void __launch_bounds__(512, 1)
 
 constexpr int kLeafStage = 200 * 1024;   // staged term tables of k_cscore_leaf
 
+// ---- measured counter tables (model blob kind 2) -----------------------------
+// Ordinal of the configuration with packed digits p in TS (ascending raw
+// order): a 32-way search, 32 probes per round by one warp.  TS must hold p.
+__device__ int64_t ts_ordinal_warp(const SearchDev &sd, uint64_t p) {
+  const int lane = threadIdx.x & 31;
+  auto raw_of = [&](uint64_t q) {
+    int64_t r = 0;
+    for (int j = 0; j < sd.sa.P; ++j) r += (int64_t)((q >> (4 * j)) & 15u) * sd.sa.stride[j];
+    return r;
+  };
+  const int64_t raw = raw_of(p);
+  int64_t lo = 0, hi = sd.N;
+  while (hi - lo > 32) {
+    const int64_t m = lo + ((hi - lo) * (lane + 1)) / 33;
+    const bool below = raw_of(__ldg(sd.packed + m)) < raw;
+    const int c = __popc(__ballot_sync(FULL, below));
+    const int64_t m_lo = __shfl_sync(FULL, m, c > 0 ? c - 1 : 0);
+    const int64_t m_hi = __shfl_sync(FULL, m, c < 32 ? c : 31);
+    if (c > 0) lo = m_lo + 1;
+    if (c < 32) hi = m_hi;
+  }
+  const bool below = lo + lane < hi && raw_of(__ldg(sd.packed + lo + lane)) < raw;
+  return lo + __popc(__ballot_sync(FULL, below));
+}
+
+// The step's set-up for a search over a counter table: its parameters,
+// Delta, the resets, and the table's row of c_profile as its "prediction".
+__global__ void __launch_bounds__(256) k_table_prep(const SearchDev *__restrict__ srch,
+                                                    StepDev *__restrict__ steps_dev,
+                                                    const __grid_constant__ StepBatch<1> sb,
+                                                    const float *__restrict__ table, int64_t Np) {
+  pdl_launch_dependents();
+  const SearchDev &sd = srch[0];
+  const StepDev &st = sb.st[0];
+  if (threadIdx.x == 0) {
+    steps_dev[0] = st;
+    sd.mm[0] = INT_MAX;
+    sd.mm[1] = INT_MIN;
+    if (st.n_out) *st.n_out = 0;
+  }
+  for (int c = threadIdx.x; c < sd.K; c += blockDim.x) sd.delta[c] = st.delta[c];
+  const int64_t n_super = ((sd.N + kSubTile - 1) / kSubTile + kSuper - 1) / kSuper;
+  for (int64_t i = threadIdx.x; i < n_super; i += blockDim.x) sd.super_sum[i] = 0;
+  if (threadIdx.x < 32) {
+    const int64_t o = ts_ordinal_warp(sd, st.cprof_packed);
+    for (int c = threadIdx.x; c < sd.K; c += 32) sd.pcprof[c] = o < sd.N ? table[(size_t)c * Np + o] : 0.0f;
+  }
+}
+
+// Rows [first, first + count) of a column table, row-major [count][K].
+__global__ void k_cols_to_rows(const float *__restrict__ cols, int64_t Np, int K, int64_t first,
+                               int64_t count, float *__restrict__ out) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= count * K) return;
+  const int64_t i = g / K;
+  const int c = (int)(g - i * K);
+  out[g] = cols[(size_t)c * Np + first + i];
+}
+
 }  // namespace
 
 void launch_leaf_cols(const uint64_t *packed, int64_t N, const uint8_t *nodes, int K, int D,
@@ -347,6 +406,23 @@ void launch_cscore(const SearchDev *srch, const float *cache, int64_t Np, int nu
   cfg.attrs = at;
   cfg.numAttrs = st != nullptr ? 1 : 0;
   cudaLaunchKernelEx(&cfg, k_cscore, srch, cache, Np);
+}
+
+}  // namespace ktune
+
+namespace ktune {
+
+void launch_table_prep(const SearchDev *srch, StepDev *steps_dev, const StepBatch<1> &sb,
+                       const float *table, int64_t Np, cudaStream_t st) {
+  k_table_prep<<<1, 256, 0, st>>>(srch, steps_dev, sb, table, Np);
+}
+const void *table_prep_func() { return reinterpret_cast<const void *>(&k_table_prep); }
+
+void launch_cols_to_rows(const float *cols, int64_t Np, int K, int64_t first, int64_t count,
+                         float *out, cudaStream_t st) {
+  const int64_t n = count * K;
+  if (n == 0) return;
+  k_cols_to_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cols, Np, K, first, count, out);
 }
 
 }  // namespace ktune

@@ -125,9 +125,17 @@ def _arr(a, dtype):
 
 # ---------------------------------------------------------------------------
 def model_blob(model: dict) -> bytes:
-    """Serialise a tree ensemble ({"roles", "trees"}) or a least-squares model
-    ({"kind": "lsq", "roles", "coef" [n_sub][K][T]}); layouts in include/ktune.h."""
+    """Serialise a tree ensemble ({"roles", "trees"}), a least-squares model
+    ({"kind": "lsq", "roles", "coef" [n_sub][K][T]}) or a measured counter table
+    ({"kind": "table", "roles", "table" [N][K] in TS order}); layouts in
+    include/ktune.h."""
     roles = model["roles"]
+    if model.get("kind") == "table":
+        table = np.ascontiguousarray(model["table"], "<f4")
+        assert table.ndim == 2 and table.shape[1] == len(roles)
+        return b"".join([struct.pack("<4I", MODEL_MAGIC, 1, 2, len(roles)),
+                         np.asarray(roles, "<i4").tobytes(),
+                         struct.pack("<Q", table.shape[0]), table.tobytes()])
     if model.get("kind") == "lsq":
         coef = np.ascontiguousarray(model["coef"], "<f4")
         assert coef.ndim == 3 and coef.shape[1] == len(roles)

@@ -66,3 +66,13 @@ def test_model_blob_layout(kt):
     assert struct.unpack("<4I", b[:16]) == (kt.MODEL_MAGIC, 1, 1, 1)
     assert len(b) == 16 + 4 + 4 + 3 * 20
     assert np.frombuffer(b[-12:], "<f4").tolist() == [0.0, 1.5, 2.5]
+
+
+def test_table_blob_layout(kt):
+    import numpy as np
+    import struct
+    t = np.arange(6, dtype=np.float32).reshape(3, 2)
+    b = kt.model_blob({"kind": "table", "roles": [0, 1], "table": t})
+    assert struct.unpack("<4I", b[:16]) == (kt.MODEL_MAGIC, 1, 2, 2)
+    assert struct.unpack("<Q", b[24:32]) == (3,)
+    assert np.frombuffer(b[32:], "<f4").tolist() == list(range(6))
