@@ -35,6 +35,21 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+LIVE_SRC = os.path.join(PKG, "live", "coulomb.cu")
+LIVE_BIN = os.path.join(PKG, "live", "coulomb_bin")
+
+
+def build_live(cc: str) -> str:
+    """The tunable kernel of the real-profile loop (paper_2102_05297_gb300.live),
+    a stand-alone program."""
+    r = subprocess.run([cc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-o", LIVE_BIN + ".tmp", LIVE_SRC],
+                       capture_output=True, text=True)
+    if r.returncode:
+        raise RuntimeError("nvcc failed on %s:\n%s%s" % (LIVE_SRC, r.stdout, r.stderr))
+    os.replace(LIVE_BIN + ".tmp", LIVE_BIN)
+    return LIVE_BIN
+
+
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -51,7 +66,9 @@ def build(verbose: bool = False, extra=()) -> str:
         return obj
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        live = ex.submit(build_live, cc)
         objs = list(ex.map(one, sources()))
+        live.result()
     tmp = LIB + ".tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode:
