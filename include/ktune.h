@@ -452,7 +452,8 @@ int ktune_model_from_mlp(ktune_mlp *m, ktune_model **out);
  * counterpart in the paper): C[M][N] = A[M][Kd] * B[N][Kd]^T, all device
  * buffers, A and B bfloat16 bit patterns (uint16) row-major with leading
  * dimensions lda, ldb (multiples of 8, 16-byte aligned rows), C float32 with
- * leading dimension ldc; Kd a multiple of 16; N a multiple of 16.  Enqueued
+ * leading dimension ldc (a multiple of 4, 16-byte aligned); Kd a multiple of
+ * 16; N a multiple of 16.  Enqueued
  * on `stream`, then synchronised (the call reports a tensor-core wait that
  * timed out as KTUNE_ETIMEOUT). */
 int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, float *C, int ldc,

@@ -80,6 +80,13 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) 
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Groups of copies: commit the copies issued so far as one group; wait until
+// at most N of this thread's groups are still pending.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Programmatic dependent launch: wait until the grids this one depends on
 // have completed and their memory is visible (a no-op when launched without

@@ -269,6 +269,7 @@ void launch_mark(uint32_t *evaluated, int64_t ordinal, cudaStream_t st);
 // ---- MLP counter model (k_mlp.cu) ----
 constexpr int kMlpHidden = 256;
 constexpr int kMlpMaxF = 256;           // feature columns (multiple of 16)
+constexpr int kMlpMaxSplits = 64;       // split-K slices of the weight-gradient GEMMs
 // weights of the pipelined forward: chunks of kMlpChunkK K-columns in the
 // shared-memory operand layout, streamed through kMlpStages stages
 constexpr int kMlpChunkK = 32;
@@ -300,6 +301,8 @@ struct EpiArgs {
   int lda = 0;
   uint16_t *at = nullptr;
   int ldat = 0;
+  size_t split_stride = 0;   // split-K (epilogue 0): slice z of c starts at c + z * split_stride
+  int ntile = 256;           // output columns per CTA (a multiple of 16, at most 256)
 };
 
 // The searches one scoring launch of the MLP serves (they share the network
@@ -354,14 +357,19 @@ void launch_mlp_pipe(int mode, const MlpDev &md, const uint64_t *packed, int64_t
                      const float *pcprof, const float *delta, const uint32_t *evaluated,
                      int *minmax, int *status, int max_ctas, cudaStream_t st);
 void launch_gemm_tc(int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
-                    int K, const EpiArgs &ep, int *status, cudaStream_t st);
+                    int K, const EpiArgs &ep, int *status, cudaStream_t st, int splits = 1);
+// out[M][N] (leading dimension ldo) = the sum, in slice order, of S slices of a
+// split-K workspace (slice z at ws + z * stride, leading dimension ldw).
+void launch_splitk_sum(const float *ws, int S, size_t stride, int ldw, int M, int N, float *out,
+                       int ldo, cudaStream_t st);
 void launch_features(const uint64_t *packed, const int *idx, int B, int P, int F, const int *off,
                      const uint16_t *utab, uint16_t *X, cudaStream_t st);
 void launch_transpose(const uint16_t *src, int lds, uint16_t *dst, int ldd, int R, int C,
                       cudaStream_t st);
 void launch_loss_grad(const float *Y, int Kp, const float *T, int K, const int *idx, int B,
                       float *G, uint16_t *Gb, uint16_t *Gbt, double *loss, cudaStream_t st);
-void launch_colsum(const float *G, int R, int C, float *out, cudaStream_t st);
+// column sums of G [R][C] into out [C]; part: scratch of ceil(R / 256) x C floats
+void launch_colsum(const float *G, int R, int C, float *out, float *part, cudaStream_t st);
 struct AdamArgs {
   float lr, b1, om1, b2, om2, eps, c1, c2;
 };
@@ -600,6 +608,7 @@ struct ktune_mlp {
   uint16_t *d_Gzb[2] = {}, *d_Gzbt[2] = {};
   double *d_loss = nullptr;
   int *d_status = nullptr;
+  float *d_ws = nullptr;                // split-K workspace of the weight gradients
   // prediction staging
   uint64_t *d_pred_in = nullptr;
   float *d_pred_out = nullptr;

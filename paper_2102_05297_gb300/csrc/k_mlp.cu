@@ -50,17 +50,18 @@ __device__ __forceinline__ uint4 pack8(const uint16_t *h) {
 }
 
 // Rows [0, rows) x columns [k0, k0 + kc) of a bf16 row-major matrix into
-// shared memory in the core-matrix layout with KC = kc; rows >= valid are 0.
-// kc is a multiple of 16; ld a multiple of 8; src 16-byte aligned.
+// shared memory in the core-matrix layout with KC = kc, by asynchronous
+// 16-byte copies; rows >= valid are 0.  kc is a multiple of 16; ld a multiple
+// of 8; src 16-byte aligned.
 __device__ __forceinline__ void load_tile(uint8_t *dst, const uint16_t *src, int ld, int rows,
                                           int valid, int k0, int kc) {
   const int per_row = kc >> 3;
   const int pieces = rows * per_row;
   for (int p = threadIdx.x; p < pieces; p += blockDim.x) {
     const int r = p / per_row, kb = p - r * per_row;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (r < valid) v = __ldg(reinterpret_cast<const uint4 *>(src + (size_t)r * ld + k0 + kb * 8));
-    *reinterpret_cast<uint4 *>(dst + tc::core_off(r, kb * 8, kc)) = v;
+    uint8_t *d = dst + tc::core_off(r, kb * 8, kc);
+    if (r < valid) cp_async16(d, src + (size_t)r * ld + k0 + kb * 8);
+    else *reinterpret_cast<uint4 *>(d) = make_uint4(0, 0, 0, 0);
   }
 }
 
@@ -77,21 +78,40 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, const uint8_t *sA, in
   }
 }
 
-constexpr int kGemmSmem = 16384 + 32768 + 65536;   // pads to two CTAs per SM (2 x 256 TMEM columns)
+constexpr int kGemmStage = 16384 + 32768;         // A 128 x 64 and B 256 x 64 bf16
+constexpr int kGemmSmem = 2 * kGemmStage;          // two stages: two CTAs per SM (2 x 256 TMEM columns)
 
+// 16 floats (v) of one row into dst (16-byte aligned): four vector stores.
+__device__ __forceinline__ void store16f(float *dst, const float (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+__device__ __forceinline__ void store16h(uint16_t *dst, const uint16_t (&h)[16]) {
+  reinterpret_cast<uint4 *>(dst)[0] = pack8(h);
+  reinterpret_cast<uint4 *>(dst)[1] = pack8(h + 8);
+}
+
+// C = A * B^T over K range of split blockIdx.z: the K chunks of 64 run through
+// two shared-memory stages, the copies of chunk c + 1 in flight while the
+// tensor cores work on chunk c.  Epilogue per 16 accumulator columns of a row:
+// vector stores of the row-major outputs, and for the transposes one 2-byte
+// store per lane (consecutive rows of a column: coalesced across the warp).
 template <int EPI>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const uint16_t *__restrict__ A, int lda, const uint16_t *__restrict__ B, int ldb,
               int M, int N, int K, EpiArgs ep, int *status) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t *sA = sm;            // 128 x 64 bf16
-  uint8_t *sB = sm + 16384;    // 256 x 64 bf16
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5;
   const int m0 = blockIdx.x * 128;
-  const int n0 = blockIdx.y * 256;
-  const int Nt = N - n0 < 256 ? N - n0 : 256;
+  const int n0 = blockIdx.y * ep.ntile;
+  const int Nt = N - n0 < ep.ntile ? N - n0 : ep.ntile;
+  // this split's K range, in whole chunks of 64
+  const int n_chunks = (K + 63) / 64;
+  const int c_lo = (int)((int64_t)n_chunks * blockIdx.z / gridDim.z);
+  const int c_hi = (int)((int64_t)n_chunks * (blockIdx.z + 1) / gridDim.z);
   if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
   if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
   tc::fence_before();
@@ -100,60 +120,105 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = tmem_base;
   uint32_t phase = 0;
   bool ok = true;
-  for (int k0 = 0; k0 < K; k0 += 64) {
-    const int kc = K - k0 < 64 ? K - k0 : 64;
-    load_tile(sA, A + (size_t)m0 * lda, lda, 128, M - m0, k0, kc);
-    load_tile(sB, B + (size_t)n0 * ldb, ldb, Nt, Nt, k0, kc);
+  auto stage_a = [&](int c) { return sm + (c & 1) * kGemmStage; };
+  auto stage_b = [&](int c) { return sm + (c & 1) * kGemmStage + 16384; };
+  auto issue = [&](int c) {
+    const int k0 = c * 64, kc = K - k0 < 64 ? K - k0 : 64;
+    load_tile(stage_a(c), A + (size_t)m0 * lda, lda, 128, M - m0, k0, kc);
+    load_tile(stage_b(c), B + (size_t)n0 * ldb, ldb, Nt, Nt, k0, kc);
+    cp_async_commit();
+  };
+  if (c_lo < c_hi) issue(c_lo);
+  for (int c = c_lo; c < c_hi; ++c) {
+    // the MMAs of chunk c - 1 read the stage chunk c + 1 is copied into
+    if (c > c_lo) {
+      const bool w = tc::mbar_wait(&mbar, phase, kWaitLimit);
+      if (w) phase ^= 1;
+      tc::fence_after();
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
+    }
+    if (c + 1 < c_hi) {
+      issue(c + 1);
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
     tc::fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
       tc::fence_after();
-      issue_chunk(tmem, sA, kc, 0, sB, kc, Nt, k0 == 0);
+      const int kc = K - c * 64 < 64 ? K - c * 64 : 64;
+      issue_chunk(tmem, stage_a(c), kc, 0, stage_b(c), kc, Nt, c == c_lo);
       tc::mma_commit(&mbar);
     }
-    ok = tc::mbar_wait(&mbar, phase, kWaitLimit);
-    phase ^= 1;
-    tc::fence_after();
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
   }
+  if (ok && c_lo < c_hi) {
+    const bool w = tc::mbar_wait(&mbar, phase, kWaitLimit);
+    if (w) phase ^= 1;
+    tc::fence_after();
+    ok = __syncthreads_and(w);
+  }
+  cp_async_wait_all();
   if (!ok) {
-    tc::mbar_wait(&mbar, phase ^ 1, kWaitLimit);
+    tc::mbar_wait(&mbar, phase, kWaitLimit);   // the MMAs still in flight, if any
     if (threadIdx.x == 0) atomicExch(status, KTUNE_ETIMEOUT);
   } else {
     const int row = m0 + threadIdx.x;
+    float *cz = ep.c ? ep.c + blockIdx.z * ep.split_stride : nullptr;
     for (int c0 = 0; c0 < Nt; c0 += 16) {
       float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (row >= M) continue;
+      if (c_lo < c_hi) {
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = n0 + c0 + i;
-        if (EPI == 0) {
-          ep.c[(size_t)row * ep.ldc + c] = v[i];
-        } else if (EPI == 1) {
-          const float z = __fadd_rn(v[i], ep.bias[c]);
-          ep.z[(size_t)row * ep.ldz + c] = z;
-          const uint16_t h = tc::f2bf(gelu_f(z));
-          ep.a[(size_t)row * ep.lda + c] = h;
-          if (ep.at) ep.at[(size_t)c * ep.ldat + row] = h;
-        } else if (EPI == 2) {
-          ep.c[(size_t)row * ep.ldc + c] = __fadd_rn(v[i], ep.bias[c]);
-        } else {
-          const float g = __fmul_rn(v[i], gelu_grad_f(ep.z[(size_t)row * ep.ldz + c]));
-          ep.c[(size_t)row * ep.ldc + c] = g;
-          const uint16_t h = tc::f2bf(g);
-          ep.a[(size_t)row * ep.lda + c] = h;
-          if (ep.at) ep.at[(size_t)c * ep.ldat + row] = h;
+        for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+      }
+      if (row >= M) continue;
+      const int cb = n0 + c0;
+      if (EPI == 0) {
+        store16f(cz + (size_t)row * ep.ldc + cb, v);
+      } else if (EPI == 2) {
+        float o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[i] = __fadd_rn(v[i], ep.bias[cb + i]);
+        store16f(ep.c + (size_t)row * ep.ldc + cb, o);
+      } else {
+        float o[16];
+        uint16_t h[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (EPI == 1) {
+            o[i] = __fadd_rn(v[i], ep.bias[cb + i]);                  // the pre-activation
+            h[i] = tc::f2bf(gelu_f(o[i]));
+          } else {
+            o[i] = __fmul_rn(v[i], gelu_grad_f(ep.z[(size_t)row * ep.ldz + cb + i]));
+            h[i] = tc::f2bf(o[i]);
+          }
         }
+        store16f((EPI == 1 ? ep.z + (size_t)row * ep.ldz : ep.c + (size_t)row * ep.ldc) + cb, o);
+        store16h(ep.a + (size_t)row * ep.lda + cb, h);
+        if (ep.at)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) ep.at[(size_t)(cb + i) * ep.ldat + row] = h[i];
       }
     }
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+__global__ void k_splitk_sum(const float *__restrict__ ws, int S, size_t stride, int ldw, int M, int N,
+                             float *__restrict__ out, int ldo) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)M * N) return;
+  const int r = (int)(g / N), c = (int)(g - (int64_t)r * N);
+  float t = 0.0f;
+  for (int z = 0; z < S; ++z) t = __fadd_rn(t, ws[z * stride + (size_t)r * ldw + c]);
+  out[(size_t)r * ldo + c] = t;
 }
 
 // ---- helpers ---------------------------------------------------------------------------
@@ -221,12 +286,35 @@ __global__ void k_loss_grad(const float *__restrict__ Y, int Kp, const float *__
 }
 
 // out[c] = sum over r of G[r][c] (float64 accumulation)
-__global__ void k_colsum(const float *__restrict__ G, int R, int C, float *__restrict__ out) {
+// Column sums in two passes with a fixed order.  Pass 1: CTA (bx, by) takes
+// 32 columns and 256 rows; thread (x, y) sums rows y, y + 32, ... of its
+// block in float32, then the 32 partials of a column are added in y order
+// into part[by][column].  Pass 2 adds the row blocks' partials in by order in
+// float64.  (The float64 pipe is narrow on this GPU: only pass 2 uses it.)
+constexpr int kColRows = 256;
+__global__ void __launch_bounds__(1024) k_colsum_part(const float *__restrict__ G, int R, int C,
+                                                      float *__restrict__ part) {
+  __shared__ float p[32][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * kColRows, r1 = min(R, r0 + kColRows);
+  float s = 0.0f;
+  if (c < C)
+    for (int r = r0 + threadIdx.y; r < r1; r += 32) s = __fadd_rn(s, G[(size_t)r * C + c]);
+  p[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < C) {
+    float t = 0.0f;
+    for (int y = 0; y < 32; ++y) t = __fadd_rn(t, p[y][threadIdx.x]);
+    part[(size_t)blockIdx.y * C + c] = t;
+  }
+}
+
+__global__ void k_colsum_final(const float *__restrict__ part, int nb, int C, float *__restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
-  double s = 0.0;
-  for (int r = 0; r < R; ++r) s += G[(size_t)r * C + c];
-  out[c] = (float)s;
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += (double)part[(size_t)b * C + c];
+  out[c] = (float)t;
 }
 
 // Adam on rows x cols float32 parameters (row-major); refreshes the bf16
@@ -304,9 +392,15 @@ void mlp_set_attrs(int) {
   mlp_pipe_set_attrs();
 }
 
+void launch_splitk_sum(const float *ws, int S, size_t stride, int ldw, int M, int N, float *out,
+                       int ldo, cudaStream_t st) {
+  const int64_t n = (int64_t)M * N;
+  k_splitk_sum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, S, stride, ldw, M, N, out, ldo);
+}
+
 void launch_gemm_tc(int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
-                    int K, const EpiArgs &ep, int *status, cudaStream_t st) {
-  const dim3 grid((M + 127) / 128, (N + 255) / 256);
+                    int K, const EpiArgs &ep, int *status, cudaStream_t st, int splits) {
+  const dim3 grid((M + 127) / 128, (N + ep.ntile - 1) / ep.ntile, splits);
   switch (epi) {
     case 0: k_gemm_tc<0><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status); break;
     case 1: k_gemm_tc<1><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ep, status); break;
@@ -334,8 +428,10 @@ void launch_loss_grad(const float *Y, int Kp, const float *T, int K, const int *
   k_loss_grad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Y, Kp, T, K, idx, B, G, Gb, Gbt, loss);
 }
 
-void launch_colsum(const float *G, int R, int C, float *out, cudaStream_t st) {
-  k_colsum<<<(C + 127) / 128, 128, 0, st>>>(G, R, C, out);
+void launch_colsum(const float *G, int R, int C, float *out, float *part, cudaStream_t st) {
+  const int nb = (R + kColRows - 1) / kColRows;
+  k_colsum_part<<<dim3((C + 31) / 32, nb), dim3(32, 32), 0, st>>>(G, R, C, part);
+  k_colsum_final<<<(C + 255) / 256, 256, 0, st>>>(part, nb, C, out);
 }
 
 void launch_adam(float *p, const float *g, float *m, float *v, int rows, int cols,

@@ -100,6 +100,7 @@ void enqueue_fwd_bwd(ktune_mlp *m, const int *idx, int B) {
     e.lda = H;
     e.at = m->d_At[l];
     e.ldat = B;
+    e.ntile = 64;   // 4 x more CTAs: the epilogue (GELU of every element) dominates
     launch_gemm_tc(1, a_prev, lda_prev, m->d_wb[l], l == 0 ? F : H, B, H, l == 0 ? F : H, e,
                    status, st);
     a_prev = m->d_A[l];
@@ -114,14 +115,20 @@ void enqueue_fwd_bwd(ktune_mlp *m, const int *idx, int B) {
   }
   launch_loss_grad(m->d_Y, Kp, m->d_target, m->K, idx, B, m->d_G, m->d_Gb, m->d_Gbt, m->d_loss,
                    st);
-  // layer 4
-  launch_colsum(m->d_G, B, Kp, m->d_g[7], st);
-  {
+  // weight gradients: K is the batch, split over up to 64 CTA groups, the
+  // slices summed in a fixed order
+  const int splits = std::min(kMlpMaxSplits, std::max(1, (B + 127) / 128));
+  auto wgrad = [&](const uint16_t *gt, const uint16_t *xt, int M, int N, float *out) {
     EpiArgs e;
-    e.c = m->d_g[6];
-    e.ldc = H;
-    launch_gemm_tc(0, m->d_Gbt, B, m->d_At[2], B, Kp, H, B, e, status, st);
-  }
+    e.c = m->d_ws;
+    e.ldc = N;
+    e.split_stride = (size_t)M * N;
+    launch_gemm_tc(0, gt, B, xt, B, M, N, B, e, status, st, splits);
+    launch_splitk_sum(m->d_ws, splits, (size_t)M * N, N, M, N, out, N, st);
+  };
+  // layer 4
+  launch_colsum(m->d_G, B, Kp, m->d_g[7], m->d_ws, st);
+  wgrad(m->d_Gbt, m->d_At[2], Kp, H, m->d_g[6]);
   // g_out (bf16 [B x n_out], its transpose) of the layer above, then layers 3, 2, 1
   const uint16_t *gb = m->d_Gb, *gbt = m->d_Gbt;
   int n_out = Kp;
@@ -136,17 +143,12 @@ void enqueue_fwd_bwd(ktune_mlp *m, const int *idx, int B) {
       e.lda = H;
       e.at = m->d_Gzbt[buf];
       e.ldat = B;
+      e.ntile = 64;
       // g_a(l) = g_out * W(l+1): B operand is W(l+1)^T [H x n_out]
       launch_gemm_tc(3, gb, n_out, m->d_wt[l + 1], n_out, B, H, n_out, e, status, st);
     }
-    launch_colsum(m->d_Gz[buf], B, H, m->d_g[2 * l + 1], st);
-    {
-      EpiArgs e;
-      e.c = m->d_g[2 * l];
-      e.ldc = l == 0 ? F : H;
-      const uint16_t *prev_t = l == 0 ? m->d_Xt : m->d_At[l - 1];
-      launch_gemm_tc(0, m->d_Gzbt[buf], B, prev_t, B, H, l == 0 ? F : H, B, e, status, st);
-    }
+    launch_colsum(m->d_Gz[buf], B, H, m->d_g[2 * l + 1], m->d_ws, st);
+    wgrad(m->d_Gzbt[buf], l == 0 ? m->d_Xt : m->d_At[l - 1], H, l == 0 ? F : H, m->d_g[2 * l]);
     gb = m->d_Gzb[buf];
     gbt = m->d_Gzbt[buf];
     n_out = H;
@@ -288,7 +290,8 @@ int ktune_mlp_create(ktune_space *s, int K, const int32_t *roles, const float *r
     cudaMemset(m->d_wc, 0, off);
   }
   const size_t B = (size_t)max_batch, H = kMlpHidden;
-  if ((rc = dalloc(&m->d_range, K)) || (rc = dalloc(&m->d_off, P + 1)) ||
+  if ((rc = dalloc(&m->d_ws, (size_t)kMlpMaxSplits * kMlpHidden * kMlpMaxF)) ||
+      (rc = dalloc(&m->d_range, K)) || (rc = dalloc(&m->d_off, P + 1)) ||
       (rc = dalloc(&m->d_utab, utab.size())) || (rc = dalloc(&m->d_X, B * F)) ||
       (rc = dalloc(&m->d_Xt, B * F)) || (rc = dalloc(&m->d_Y, B * m->Kp)) ||
       (rc = dalloc(&m->d_G, B * m->Kp)) || (rc = dalloc(&m->d_Gb, B * m->Kp)) ||
@@ -337,6 +340,7 @@ int ktune_mlp_destroy(ktune_mlp *m) {
     cudaFree(m->d_Gzb[b]);
     cudaFree(m->d_Gzbt[b]);
   }
+  cudaFree(m->d_ws);
   cudaFree(m->d_range);
   cudaFree(m->d_off);
   cudaFree(m->d_utab);
@@ -576,8 +580,10 @@ int ktune_gemm_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, floa
                     int M, int N, int Kd, void *stream) {
   if (!A || !B || !C) FAIL(KTUNE_EINVAL, "null argument");
   if (M < 1 || N < 16 || (N & 15) || Kd < 16 || (Kd & 15)) FAIL(KTUNE_EINVAL, "bad GEMM shape");
-  if ((lda & 7) || (ldb & 7) || lda < Kd || ldb < Kd || ldc < N) FAIL(KTUNE_EINVAL, "bad leading dimension");
-  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) FAIL(KTUNE_EINVAL, "A and B must be 16-byte aligned");
+  if ((lda & 7) || (ldb & 7) || (ldc & 3) || lda < Kd || ldb < Kd || ldc < N)
+    FAIL(KTUNE_EINVAL, "bad leading dimension");
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)C & 15))
+    FAIL(KTUNE_EINVAL, "A, B and C must be 16-byte aligned");
   int *status = nullptr;
   mlp_set_attrs(0);
   TRY(dalloc(&status, 1));
