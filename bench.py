@@ -950,7 +950,11 @@ def path_large(ctx, depth=12):
     s.close()
     t = sum(step_ms) / 1e3
     peak, _ = alu_peak(ctx["props"], ctx["pk"])
-    ach = visits / (kern_ms[1] / 1e3)
+    # the whole step is one persistent kernel (decode + filter, c_profile's
+    # prediction, walk + Eq. score, top-k): its whole duration is the divisor
+    ach = visits / (kern_ms[0] / 1e3)
+    names = ("predict_cprofile_and_decode", "summands_barrier", "walk_and_cta_topk", None, None,
+             "last_cta_slack", "select_topk")
     return {
         "workload": "large_16p on the fly: %d raw / %d valid configurations decoded every step "
                     "(none stored), K=40, depth-%d random trees, top-%d select" % (
@@ -958,13 +962,13 @@ def path_large(ctx, depth=12):
         "value": scored / t, "unit": "configs/s", "ms_per_step": 1e3 * t / n_steps,
         "steps_per_s": n_steps / t, "steps": n_steps,
         "raw_decoded_per_s": n_raw * n_steps / t,
-        "roofline": {"bound": "alu", "kernel": "k_bscore<on-the-fly> (decode + filter + walk + score)",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_step_fused<on-the-fly> (the whole step: decode + filter, c_profile "
+                               "prediction, walk + Eq. score, top-k)",
                      "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "Gvisit/s",
-                     "frac": ach / peak, "traffic": PROFILED_TRAFFIC["k_bscore_otf"],
+                     "frac": ach / peak, "traffic": PROFILED_TRAFFIC.get("k_step_fused_otf"),
                      "mean_active_counters": float(np.mean(nact)),
-                     "kernel_share": {"prepare": kern_ms[0] / kern_ms.sum(),
-                                      "score": kern_ms[1] / kern_ms.sum(),
-                                      "select": kern_ms[3] / kern_ms.sum()}},
+                     "phase_share": {n: kern_ms[1 + i] / kern_ms[0] for i, n in enumerate(names) if n}},
     }
 
 

@@ -292,8 +292,9 @@ int ktune_search_set_cached(ktune_search *search, int enable);
  * search's stream. */
 int ktune_search_set_neighbourhood(ktune_search *search, int radius);
 
-/* How whole-space steps of a tree model over a materialised space whose
- * digits fit one 32-bit word run.  shape 0: four kernels per step (prepare,
+/* How whole-space steps of a tree model over a space whose digits fit one
+ * 32-bit word run (materialised, or on the fly).  shape 0: four kernels per
+ * step (prepare,
  * score, weights, select; on a non-default stream one CUDA graph).  shape
  * 1..3: the whole step as ONE persistent kernel, a cooperative launch with one
  * CTA per SM (1: 512 threads and 8 configurations per thread per chunk, 2:
@@ -302,8 +303,13 @@ int ktune_search_set_neighbourhood(ktune_search *search, int radius);
  * bounded: a wait that gives up makes the step return KTUNE_ETIMEOUT), then
  * its warps compute the integer weights of one sub-tile each, and the CTA that
  * finishes last makes the draws (or merges the top-k lists).  Both give the
- * same scores, weights and selections bit for bit.  Shape 2 is the default for
- * the searches it applies to; other searches refuse shapes > 0 (KTUNE_ESTATE).
+ * same scores, weights and selections bit for bit.  On an on-the-fly space
+ * the persistent kernel first decodes the raw space and writes TS's one-word
+ * digits by ordinal into a scratch list of N words (so it also writes score 0
+ * for the configurations evaluated before the step, which the four kernels
+ * leave untouched there), and only shape 2 is offered (others: KTUNE_ESTATE).
+ * Shape 2 is the default for the searches it applies to; other searches
+ * refuse shapes > 0 (KTUNE_ESTATE).
  * Cached predictions and neighbourhood-restricted steps keep their own
  * kernels.  Synchronises the search's last stream. */
 int ktune_search_set_fused(ktune_search *search, int shape);

@@ -1070,8 +1070,9 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   h->cprof_raw = raw;
   h->cprof_packed = host_pack(s, raw);
   h->n_evaluated = 1;
-  const int fshape = fused_blocks_per_sm(1) >= 1 ? 2 : fused_blocks_per_sm(0) >= 1 ? 1 : 0;
-  if (m->kind == 1 && h->mode == 0 && fshape) {
+  const bool fotf = h->mode == 2 && fused_blocks_per_sm_otf() >= 1;
+  const int fshape = fotf ? 2 : fused_blocks_per_sm(1) >= 1 ? 2 : fused_blocks_per_sm(0) >= 1 ? 1 : 0;
+  if (m->kind == 1 && (h->mode == 0 || fotf) && fshape) {
     // the whole step as one persistent kernel (the default where it applies)
     const int L = 1 << m->D;
     h->fused_grid = h->num_sms;
@@ -1085,7 +1086,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
     if ((rc = dalloc(&h->d_fz_words, (size_t)m->K * L)) || (rc = dalloc(&h->d_fz_terms, (size_t)m->K * L)) ||
         (rc = dalloc(&h->d_fz_mm, 2)) || (rc = dalloc(&h->d_fz_phase, 8)) ||
         (rc = dalloc(&h->d_fz_sync, 2)) || (rc = dalloc(&h->d_fz_status, 1)) ||
-        (rc = dalloc(&h->d_fz_cand, (size_t)h->fused_grid * KTUNE_MAX_K)))
+        (rc = dalloc(&h->d_fz_cand, (size_t)h->fused_grid * KTUNE_MAX_K)) ||
+        (fotf && (rc = dalloc(&h->d_fz_list, (size_t)N))))
       return fail(rc);
     if (launch_fused_words(m->d_nodes, m->K, m->D, lay, h->d_fz_words, cs) != cudaSuccess ||
         cudaMemcpyAsync(h->d_fz_mm, mm0, 8, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
@@ -1115,7 +1117,7 @@ int ktune_search_destroy(ktune_search *h) {
   cudaFree(h->d_nbr_buf);
   cudaFree(h->d_cache);
   cudaFree(h->d_leaf_cache);
-  void *fz[] = {h->d_fz_words, h->d_fz_terms, h->d_fz_phase, h->d_fz_mm, h->d_fz_sync, h->d_fz_status, h->d_fz_cand};
+  void *fz[] = {h->d_fz_list, h->d_fz_words, h->d_fz_terms, h->d_fz_phase, h->d_fz_mm, h->d_fz_sync, h->d_fz_status, h->d_fz_cand};
   for (void *p : fz) cudaFree(p);
   void *dev[] = {h->d_eval, h->d_counters, h->d_pcprof, h->d_delta, h->d_nactive, h->d_pack,
                  h->d_s, h->d_w, h->d_subsum, h->d_supsum, h->d_cand_key, h->d_cand_raw, h->d_mm, h->d_srch,
@@ -1306,13 +1308,14 @@ static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *
     fa.sync = h->d_fz_sync;
     fa.status = h->d_fz_status;
     fa.cand = h->d_fz_cand;
+    fa.list = h->d_fz_list;
     fa.wait_ns = 1000000000ull;
     fa.phase_ns = h->timing ? h->d_fz_phase : nullptr;
     fa.four = 4;
     fa.st = sp;
     if (h->timing) CK(cudaEventRecord(h->ev[0], st));
     CK(launch_step_fused(fa, h->fused - 1, h->opts.select == KTUNE_SELECT_TOPK, h->model->D,
-                         h->fused_grid, st));
+                         h->fused_grid, st, h->mode == 2));
     if (h->timing) CK(cudaEventRecord(h->ev[1], st));
   } else if (st != nullptr && h->use_graph) {
     TRY(launch_step_graph(h, sb, st));
@@ -1701,9 +1704,11 @@ int ktune_search_set_fused(ktune_search *h, int shape) {
   if (!h) FAIL(KTUNE_EINVAL, "null search");
   if (shape < 0 || shape > fused_shapes()) FAIL(KTUNE_EINVAL, "unknown fused-kernel shape");
   if (shape > 0 && !h->d_fz_words)
-    FAIL(KTUNE_ESTATE, "the fused step needs a tree model on a materialised one-word space");
+    FAIL(KTUNE_ESTATE, "the fused step needs a tree model on a one-word space");
   if (shape > 0 && fused_blocks_per_sm(shape - 1) < 1)
     FAIL(KTUNE_ESTATE, "this kernel shape cannot be resident on this device");
+  if (shape > 0 && h->mode == 2 && shape != 2)
+    FAIL(KTUNE_ESTATE, "on-the-fly spaces take the fused step in shape 2 only");
   CK(cudaStreamSynchronize(h->last_stream));
   h->fused = shape;
   return KTUNE_OK;

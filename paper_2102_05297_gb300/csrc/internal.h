@@ -194,6 +194,7 @@ struct FusedArgs {
   unsigned long long *sync;       // [2] grid-barrier arrivals, completions (only ever grow)
   int *status;                    // KTUNE_ETIMEOUT when a barrier wait gave up
   uint64_t *cand;                 // [grid][KTUNE_MAX_K] per-CTA top-k keys
+  uint32_t *list;                 // on-the-fly spaces: the step's one-word digits of TS by ordinal
   uint64_t wait_ns;               // limit of each barrier wait
   uint64_t *phase_ns;             // [8] phase time stamps (null: none taken)
   uint32_t four;                  // 4, as a launch parameter (the walk's word-offset multiplier)
@@ -201,8 +202,9 @@ struct FusedArgs {
 };
 int fused_shapes();
 int fused_blocks_per_sm(int shape);
+int fused_blocks_per_sm_otf();
 cudaError_t launch_step_fused(const FusedArgs &fa, int shape, bool topk, int D, int grid,
-                              cudaStream_t st);
+                              cudaStream_t st, bool otf);
 cudaError_t launch_fused_words(const uint8_t *nodes, int K, int D, const PrepArgs &lay,
                                uint32_t *words, cudaStream_t st);
 
@@ -540,6 +542,7 @@ struct ktune_search {
   unsigned long long *d_fz_sync = nullptr;
   int *d_fz_status = nullptr;
   uint64_t *d_fz_cand = nullptr;       // [grid][KTUNE_MAX_K]
+  uint32_t *d_fz_list = nullptr;       // on-the-fly spaces: TS's one-word digits, rebuilt each step
   // device buffers
   uint32_t *d_eval = nullptr;
   float *d_counters = nullptr, *d_pcprof = nullptr, *d_delta = nullptr;

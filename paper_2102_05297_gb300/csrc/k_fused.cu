@@ -32,6 +32,7 @@
 #include "device_common.cuh"
 #include "internal.h"
 #include "step_common.cuh"
+#include "otf.cuh"
 
 namespace ktune {
 
@@ -480,10 +481,101 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   return sh_n;
 }
 
+// Packed digits (4 bits per parameter) of a one-word configuration.
+__device__ __forceinline__ uint64_t packed_of_word(const SearchDev &sd, uint32_t W) {
+  uint64_t p = 0;
+  for (int j = 0; j < sd.sa.P; ++j)
+    p |= (uint64_t)((W >> sd.pos[j]) & ((1u << sd.width[j]) - 1u)) << (4 * j);
+  return p;
+}
+
+// PD of the fused step over an on-the-fly space: every CTA decodes its range
+// of raw tiles (4096 raw indices each; a warp takes whole tiles, a lane four
+// consecutive indices of each round of 128, by odometer steps), checks the
+// constraints, and writes the one-word digits of every valid configuration
+// at its ordinal in fa.list (the tile's valid prefix plus its rank, counted
+// with warp scans).  TS is thus rebuilt in every step, never kept.
+__device__ __noinline__ void fused_decode(const FusedArgs &fa) {
+  const SearchDev &sd = fa.sd;
+  OtfCtx *ctx = reinterpret_cast<OtfCtx *>(fz_smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  if (threadIdx.x < KTUNE_MAX_PARAMS) {
+    const int j = threadIdx.x;
+    ctx->pos[j] = sd.pos[j];
+    ctx->width[j] = sd.width[j];
+    ctx->radix[j] = (uint8_t)sd.sa.radix[j];
+    ctx->inc[j] = sd.inc128[j];
+    ctx->cis[j] = sd.ci_stride[j];
+  }
+  for (int i = threadIdx.x; i < (int)(sizeof(ctx->win) / 4); i += blockDim.x)
+    reinterpret_cast<uint32_t *>(ctx->win)[i] = reinterpret_cast<const uint32_t *>(sd.win)[i];
+  if (threadIdx.x == 0) {
+    int top = sd.sa.P;
+    for (int j = 0; j < sd.sa.P; ++j)
+      if (sd.inc128[j]) {
+        top = j;
+        break;
+      }
+    ctx->P = sd.sa.P;
+    ctx->n_win = sd.n_win;
+    ctx->n_generic = sd.n_generic;
+    ctx->inc_top = top;
+    ctx->ci_words = sd.ci_table ? sd.ci_words : 0;
+  }
+  uint32_t *tab = reinterpret_cast<uint32_t *>(ctx + 1);
+  if (sd.ci_table)
+    for (int i = threadIdx.x; i < sd.ci_words; i += blockDim.x) tab[i] = __ldg(sd.ci_table + i);
+  else
+    for (int i = threadIdx.x; i < sd.win_words; i += blockDim.x) tab[i] = __ldg(sd.win_table + i);
+  __syncthreads();
+  const uint32_t n_raw = (uint32_t)sd.sa.n_raw;
+  const int64_t n_tiles = (sd.sa.n_raw + kEnumTileRaw - 1) / kEnumTileRaw;
+  const int64_t t_lo = n_tiles * blockIdx.x / gridDim.x, t_hi = n_tiles * (blockIdx.x + 1) / gridDim.x;
+  const bool use_ci = ctx->ci_words > 0;
+  uint32_t *__restrict__ list = fa.list;
+  for (int64_t t = t_lo + warp; t < t_hi; t += NW) {
+    const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
+    int64_t ord = __ldg(sd.tile_offset + t);
+    uint32_t W = otf_decode(ctx, tbase + 4u * (uint32_t)lane);
+    uint32_t xci = use_ci ? otf_ci(ctx, W) : 0u;
+    for (int q = 0; q < kEnumTileRaw / 128; ++q) {
+      const uint32_t rb = tbase + (uint32_t)q * 128u;
+      if (rb >= n_raw) break;                       // warp-uniform
+      const uint32_t r0 = rb + 4u * (uint32_t)lane;
+      const int n_here = r0 >= n_raw ? 0 : (int)min(4u, n_raw - r0);
+      uint32_t Wq[4];
+      uint32_t vm = 0;
+      Wq[0] = W;
+      if (use_ci) {
+        uint32_t x = xci;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u > 0) Wq[u] = otf_next_ci(ctx, Wq[u - 1], x);
+          if (u < n_here && ((tab[x >> 5] >> (x & 31)) & 1u)) vm |= 1u << u;
+        }
+      } else {
+#pragma unroll
+        for (int u = 1; u < 4; ++u) Wq[u] = otf_next(ctx, Wq[u - 1]);
+        vm = otf_valid4(ctx, sd, Wq, n_here);
+      }
+      const uint32_t cnt = __popc(vm);
+      const uint32_t incl = warp_incl(cnt);
+      const uint32_t tot = __shfl_sync(kFullMask, incl, 31);
+      uint32_t slot = incl - cnt;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if ((vm >> u) & 1u) list[ord + slot++] = Wq[u];
+      ord += tot;
+      W = otf_add128(ctx, W, xci);
+    }
+  }
+}
+
 template <int THREADS, int DT, bool TOPK>
 struct Scorer {
   static constexpr int NW = THREADS / 32;
   const SearchDev &sd;
+  const uint32_t *words;   // the one-word digits of TS by ordinal
   int nt, D, L, k;
   uint32_t four;
   bool first, last;
@@ -494,7 +586,7 @@ struct Scorer {
   // configurations base + c * THREADS + threadIdx.x, c < CPT, below hi
   template <int CPT>
   __device__ __forceinline__ void chunk(int64_t base, int64_t hi) {
-    const uint32_t *__restrict__ narrow_p = sd.narrow;
+    const uint32_t *__restrict__ narrow_p = words;
     const uint32_t *__restrict__ eval_p = sd.eval;
     float *__restrict__ s_p = sd.s;
     uint32_t W[CPT];
@@ -505,7 +597,7 @@ struct Scorer {
     for (int c = 0; c < CPT; ++c) {
       const int64_t i = base + (int64_t)c * THREADS + threadIdx.x;
       ok[c] = i < hi;
-      W[c] = ok[c] ? __ldg(narrow_p + i) : 0u;
+      W[c] = ok[c] ? __ldcg(narrow_p + i) : 0u;   // (on the fly: written earlier in this kernel)
       s[c] = (first || !ok[c]) ? 0.0f : __ldcg(s_p + i);
       ev[c] = (last && ok[c]) ? (__ldg(eval_p + (i >> 5)) >> (i & 31)) & 1u : 0u;
     }
@@ -540,7 +632,7 @@ struct Scorer {
   }
 };
 
-template <int THREADS, int CPT, int DT, bool TOPK>
+template <int THREADS, int CPT, int DT, bool TOPK, bool OTF>
 __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant__ FusedArgs fa) {
   uint8_t *smem = fz_smem;
   constexpr int NW = THREADS / 32;
@@ -562,8 +654,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   stamp(fa, 0, cta0);
   const int64_t lo = N * (int64_t)blockIdx.x / G, hi = N * (int64_t)(blockIdx.x + 1) / G;
   // this CTA's digits and evaluated bits, brought into L2 while c_profile's walk runs
-  for (int64_t off = (int64_t)threadIdx.x * 32; off < hi - lo; off += (int64_t)THREADS * 32)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.narrow + lo + off));
+  if (!OTF)
+    for (int64_t off = (int64_t)threadIdx.x * 32; off < hi - lo; off += (int64_t)THREADS * 32)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.narrow + lo + off));
   for (int64_t off = (int64_t)threadIdx.x * 32; off < (hi - lo) / 32 + 1; off += (int64_t)THREADS * 32)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.eval + (lo >> 5) + off));
   // ---- P0: c_profile's prediction per counter, the active counters ----------------
@@ -600,6 +693,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   }
   __syncthreads();
   const int n_active = sh_nact;
+  if constexpr (OTF) {   // TS of this step, rebuilt by decoding the raw space
+    fused_decode(fa);
+    __syncthreads();
+  }
   if (blockIdx.x == 0) {
     for (int p = threadIdx.x; p < K; p += THREADS) {
       sd.pcprof[p] = sh_A[p];
@@ -646,8 +743,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   const int n_groups = max(1, (n_active + per_group - 1) / per_group);
   uint32_t *trees = reinterpret_cast<uint32_t *>(smem);
   uint64_t *lists = reinterpret_cast<uint64_t *>(smem + kFusedSmem - kListBytes);
-  Scorer<THREADS, DT, TOPK> sc{sd, 0, D, L, k, fa.four, true, false, FLT_MAX, -FLT_MAX, false,
-                               lists + warp * KTUNE_MAX_K};
+  Scorer<THREADS, DT, TOPK> sc{sd, OTF ? fa.list : sd.narrow, 0, D, L, k, fa.four, true, false,
+                               FLT_MAX, -FLT_MAX, false, lists + warp * KTUNE_MAX_K};
   if (TOPK)
     for (int e = lane; e < KTUNE_MAX_K; e += 32) sc.tk[e] = 0ull;
   for (int g = 0; g < n_groups; ++g) {
@@ -764,7 +861,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   const int count = sh_count;
   if ((int)threadIdx.x < count) {
     const int j = threadIdx.x;
-    const uint64_t p = __ldg(sd.packed + pick[j]);
+    const uint64_t p = OTF ? packed_of_word(sd, __ldcg(fa.list + pick[j])) : __ldg(sd.packed + pick[j]);
     if (!TOPK) pick_s[j] = __ldcg(sd.s + pick[j]);
     int64_t raw = 0;
     for (int q = 0; q < sd.sa.P; ++q) raw += (int64_t)nib64(p, q) * sd.sa.stride[q];
@@ -784,7 +881,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
 
 // The shared-memory opt-in of one kernel, once per device (the static flag
 // belongs to this kernel's instantiation).
-template <int THREADS, int CPT, int DT, bool TOPK>
+template <int THREADS, int CPT, int DT, bool TOPK, bool OTF>
 cudaError_t smem_opt_in() {
   static std::atomic<uint64_t> done{0};   // bit d: set on device d
   int dev = 0;
@@ -792,16 +889,16 @@ cudaError_t smem_opt_in() {
   if (e != cudaSuccess) return e;
   const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (done.load() & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_step_fused<THREADS, CPT, DT, TOPK>,
+  e = cudaFuncSetAttribute(k_step_fused<THREADS, CPT, DT, TOPK, OTF>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
   if (e == cudaSuccess && bit) done.fetch_or(bit);
   return e;
 }
 
-template <int THREADS, int CPT, int DT, bool TOPK>
+template <int THREADS, int CPT, int DT, bool TOPK, bool OTF>
 cudaError_t launch_fused_t(const FusedArgs &fa, int grid, cudaStream_t st) {
-  auto kern = k_step_fused<THREADS, CPT, DT, TOPK>;
-  cudaError_t e = smem_opt_in<THREADS, CPT, DT, TOPK>();
+  auto kern = k_step_fused<THREADS, CPT, DT, TOPK, OTF>;
+  cudaError_t e = smem_opt_in<THREADS, CPT, DT, TOPK, OTF>();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -816,20 +913,20 @@ cudaError_t launch_fused_t(const FusedArgs &fa, int grid, cudaStream_t st) {
   return cudaLaunchKernelEx(&cfg, kern, fa);
 }
 
-template <int THREADS, int CPT, bool TOPK>
+template <int THREADS, int CPT, bool TOPK, bool OTF = false>
 cudaError_t launch_fused_d(const FusedArgs &fa, int D, int grid, cudaStream_t st) {
   switch (D) {
-    case 12: return launch_fused_t<THREADS, CPT, 12, TOPK>(fa, grid, st);
-    case 8: return launch_fused_t<THREADS, CPT, 8, TOPK>(fa, grid, st);
-    default: return launch_fused_t<THREADS, CPT, 0, TOPK>(fa, grid, st);
+    case 12: return launch_fused_t<THREADS, CPT, 12, TOPK, OTF>(fa, grid, st);
+    case 8: return launch_fused_t<THREADS, CPT, 8, TOPK, OTF>(fa, grid, st);
+    default: return launch_fused_t<THREADS, CPT, 0, TOPK, OTF>(fa, grid, st);
   }
 }
 
-template <int THREADS, int CPT, int DT, bool TOPK>
+template <int THREADS, int CPT, int DT, bool TOPK, bool OTF = false>
 int blocks_per_sm_t() {
   int b = 0;
-  auto kern = k_step_fused<THREADS, CPT, DT, TOPK>;
-  if (smem_opt_in<THREADS, CPT, DT, TOPK>() != cudaSuccess) return 0;
+  auto kern = k_step_fused<THREADS, CPT, DT, TOPK, OTF>;
+  if (smem_opt_in<THREADS, CPT, DT, TOPK, OTF>() != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, THREADS, kFusedSmem) != cudaSuccess) return 0;
   return b;
 }
@@ -850,8 +947,15 @@ int fused_blocks_per_sm(int shape) {
   }
 }
 
+int fused_blocks_per_sm_otf() {
+  return std::min(blocks_per_sm_t<1024, 4, 0, false, true>(), blocks_per_sm_t<1024, 4, 0, true, true>());
+}
+
 cudaError_t launch_step_fused(const FusedArgs &fa, int shape, bool topk, int D, int grid,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool otf) {
+  if (otf)   // on-the-fly spaces: shape 2 (1024 threads, 4 configurations per thread) only
+    return topk ? launch_fused_d<1024, 4, true, true>(fa, D, grid, st)
+                : launch_fused_d<1024, 4, false, true>(fa, D, grid, st);
   switch (shape) {
     case 1:
       return topk ? launch_fused_d<1024, 4, true>(fa, D, grid, st) : launch_fused_d<1024, 4, false>(fa, D, grid, st);

@@ -183,16 +183,19 @@ def test_every_score_and_weight_general_walk(kt):
     run(kt, d, model, steps=4, seed=3, fseed=5)
 
 
-@pytest.mark.parametrize("name,select,k", [("batch_3", "sample", 7), ("batch_6", "sample", 6),
-                                           ("batch_5", "topk", 16)])
-def test_every_score_on_the_fly(kt, name, select, k):
-    """On-the-fly spaces score by ordinal without storing TS; entries of
-    configurations evaluated before the step are not written there."""
+@pytest.mark.parametrize("name,select,k,fused", [("batch_3", "sample", 7, 0), ("batch_6", "sample", 6, 0),
+                                                 ("batch_5", "topk", 16, 0), ("batch_3", "sample", 7, 2),
+                                                 ("batch_6", "sample", 6, 2), ("batch_5", "topk", 16, 2),
+                                                 ("batch_0", "topk", 5, 2)])
+def test_every_score_on_the_fly(kt, name, select, k, fused):
+    """On-the-fly spaces score by ordinal without storing TS (the four-kernel
+    chain writes no score for configurations evaluated before the step; the
+    fused step decodes TS into a per-step list and writes 0 for them)."""
     d = W.load_space(name)
     roles = W.layout(32)
     model = random_model(d.radices, roles, depth=11, seed=7)
     run(kt, d, model, steps=4, k=k, seed=9, select=select, flags=kt.KTUNE_ON_THE_FLY, fseed=7,
-        zero_evaluated=False)
+        zero_evaluated=bool(fused), fused=fused)
 
 
 def test_readback_rules(kt):

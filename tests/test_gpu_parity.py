@@ -280,20 +280,22 @@ def test_steps_topk(kt, name, K, depth, k):
 
 # batch_6's constrained parameters have 270,336 value combinations, more than
 # the constrained-index table holds: it exercises the window-table check
-@pytest.mark.parametrize("name,select,k", [("tiny", "sample", 5), ("batch_3", "sample", 7),
-                                           ("batch_5", "topk", 16), ("batch_0", "topk", 5),
-                                           ("batch_6", "sample", 6), ("batch_6", "topk", 9)])
-def test_steps_on_the_fly(kt, name, select, k):
+@pytest.mark.parametrize("name,select,k,fused", [("tiny", "sample", 5, None), ("batch_3", "sample", 7, None),
+                                                 ("batch_5", "topk", 16, None), ("batch_0", "topk", 5, None),
+                                                 ("batch_6", "sample", 6, None), ("batch_6", "topk", 9, None),
+                                                 ("batch_6", "topk", 9, 0), ("tiny", "sample", 5, 0)])
+def test_steps_on_the_fly(kt, name, select, k, fused):
     d = W.space_tiny_block_tile() if name == "tiny" else W.load_space(name)
     roles = W.layout(32)
     model = random_model(d.radices, roles, depth=11, seed=7)
     gpu, cnt, rt = _synthetic(d, roles, 7)
     out = run_pair(d, model, cnt, steps=5, k=k, seed=9, select=select, runtime_fn=rt, kt=kt,
-                   flags=kt.KTUNE_ON_THE_FLY)
+                   flags=kt.KTUNE_ON_THE_FLY, fused=fused)
     _check(out)
 
 
-def test_on_the_fly_matches_materialised(kt):
+@pytest.mark.parametrize("fused", [0, 2])
+def test_on_the_fly_matches_materialised(kt, fused):
     d = W.load_space("batch_6")
     roles = W.layout(16)
     model = random_model(d.radices, roles, depth=9, seed=2)
@@ -302,6 +304,8 @@ def test_on_the_fly_matches_materialised(kt):
         sp = kt.Space.from_desc(d, flags=flags)
         m = kt.Model(sp, model)
         s = kt.Search(sp, m, k=8, seed=3)
+        if flags == kt.KTUNE_ON_THE_FLY:
+            s.set_fused(fused)
         gpu, cnt, rt = _synthetic(d, roles, 1)
         seq = []
         for _ in range(4):
@@ -422,3 +426,11 @@ def test_fused_step_refused_where_it_does_not_apply(kt):
     with pytest.raises(kt.KtuneError) as e:
         s2.set_fused(7)
     assert e.value.code == kt.KTUNE_EINVAL
+    sp3 = kt.Space.from_desc(d2, flags=kt.KTUNE_ON_THE_FLY)
+    s3 = kt.Search(sp3, kt.Model(sp3, random_model(d2.radices, W.layout(16), depth=5, seed=1)), k=5)
+    for shape in (1, 3):
+        with pytest.raises(kt.KtuneError) as e:
+            s3.set_fused(shape)
+        assert e.value.code == kt.KTUNE_ESTATE
+    s3.set_fused(0)
+    s3.set_fused(2)
