@@ -966,13 +966,16 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
       (rc = dalloc(&h->d_out_packed, KTUNE_MAX_K)) || (rc = dalloc(&h->d_nout, 1)))
     return fail(rc);
   if (cudaMallocHost((void **)&h->h_counters, KTUNE_MAX_COUNTERS * 4) != cudaSuccess ||
-      cudaMallocHost((void **)&h->h_out_raw, KTUNE_MAX_K * 8) != cudaSuccess ||
-      cudaMallocHost((void **)&h->h_out_score, KTUNE_MAX_K * 4) != cudaSuccess ||
-      cudaMallocHost((void **)&h->h_out_packed, KTUNE_MAX_K * 8) != cudaSuccess ||
+      cudaHostAlloc((void **)&h->hout, sizeof(HostOut), cudaHostAllocMapped) != cudaSuccess ||
       cudaMallocHost((void **)&h->h_nout, 8) != cudaSuccess) {
     set_error("pinned host allocation failed");
     return fail(KTUNE_ENOMEM);
   }
+  if (cudaHostGetDevicePointer((void **)&h->hout_dev, h->hout, 0) != cudaSuccess) {
+    set_error("mapped host memory is not addressable by the device");
+    return fail(KTUNE_ECUDA);
+  }
+  memset(h->hout, 0, sizeof(HostOut));
   SearchDev &sd = h->sdh;
   sd.packed = s->d_packed;
   sd.narrow = s->d_narrow;
@@ -1124,7 +1127,7 @@ int ktune_search_destroy(ktune_search *h) {
                  h->d_steps, h->d_items, h->d_sub_search, h->d_out_raw, h->d_out_score,
                  h->d_out_packed, h->d_nout};
   for (void *p : dev) cudaFree(p);
-  void *pin[] = {h->h_counters, h->h_out_raw, h->h_out_score, h->h_out_packed, h->h_nout};
+  void *pin[] = {h->h_counters, h->hout, h->h_nout};
   for (void *p : pin) cudaFreeHost(p);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -1285,7 +1288,8 @@ static int fused_status(ktune_search *h) {
 }
 
 static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *out_raw,
-                        float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st) {
+                        float *out_score, uint64_t *out_packed, int *n_out, cudaStream_t st,
+                        int *status_out = nullptr) {
   StepBatch<1> sb{};
   StepDev &sp = sb.st[0];
   sp.cprof_packed = h->cprof_packed;
@@ -1307,6 +1311,7 @@ static int enqueue_step(ktune_search *h, const float *counters, int k, int64_t *
     fa.mm_live = h->d_fz_mm;
     fa.sync = h->d_fz_sync;
     fa.status = h->d_fz_status;
+    fa.status_out = status_out;
     fa.cand = h->d_fz_cand;
     fa.list = h->d_fz_list;
     fa.wait_ns = 1000000000ull;
@@ -1336,12 +1341,12 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
   const int K = h->model->K;
   for (int i = 0; i < K; ++i)
     if (!isfinite(counters[i])) FAIL(KTUNE_EINVAL, "non-finite profiled counter");
-  TRY(enqueue_step(h, counters, k, h->d_out_raw, h->d_out_score, h->d_out_packed, h->d_nout,
-                   h->stream));
-  CK(cudaMemcpyAsync(h->h_out_raw, h->d_out_raw, k * 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h->h_out_score, h->d_out_score, k * 4, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h->h_out_packed, h->d_out_packed, k * 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h->h_nout, h->d_nout, 4, cudaMemcpyDeviceToHost, h->stream));
+  // the step's kernels write the outputs (and the fused step its barrier
+  // status) into the mapped host block: no copies after the launch
+  HostOut *ho = h->hout, *hd = h->hout_dev;
+  ho->fused_status = 0;
+  TRY(enqueue_step(h, counters, k, hd->raw, hd->score, hd->packed, &hd->n_out, h->stream,
+                   &hd->fused_status));
   if (h->model->kind == 2)
     CK(cudaMemcpyAsync(h->h_nout + 1, h->model->mlp->d_status, 4, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1349,13 +1354,13 @@ int ktune_step(ktune_search *h, const float *counters, int k, int64_t *out_raw, 
     cudaMemset(h->model->mlp->d_status, 0, 4);
     FAIL(KTUNE_ETIMEOUT, "a tensor-core wait of the MLP timed out");
   }
-  TRY(fused_status(h));
-  const int n = *h->h_nout;
+  if (h->last_fused && ho->fused_status) FAIL(KTUNE_ETIMEOUT, "a grid-barrier wait of the fused step timed out");
+  const int n = ho->n_out;
   *n_out = n;
-  memcpy(out_raw, h->h_out_raw, n * 8);
-  memcpy(out_score, h->h_out_score, n * 4);
-  h->last_raw.assign(h->h_out_raw, h->h_out_raw + n);
-  h->last_packed.assign(h->h_out_packed, h->h_out_packed + n);
+  memcpy(out_raw, ho->raw, n * 8);
+  memcpy(out_score, ho->score, n * 4);
+  h->last_raw.assign(ho->raw, ho->raw + n);
+  h->last_packed.assign(ho->packed, ho->packed + n);
   h->n_evaluated += n;
   if (h->nbr_radius) {
     if (n == 0) FAIL(KTUNE_EXHAUSTED, "no unevaluated valid configuration in the neighbourhood");

@@ -173,6 +173,17 @@ struct SearchDev {
 };
 
 // Per-step inputs and outputs of one search.
+// The outputs of one ktune_step in mapped pinned host memory: the step's
+// kernels write them straight to the host, so that the call needs no copies
+// after the launch, only the stream's synchronisation.
+struct HostOut {
+  int64_t raw[KTUNE_MAX_K];
+  uint64_t packed[KTUNE_MAX_K];
+  float score[KTUNE_MAX_K];
+  int n_out;
+  int fused_status;   // the fused step's barrier status (KTUNE_ETIMEOUT when a wait gave up)
+};
+
 struct StepDev {
   uint64_t cprof_packed;
   int64_t *out_raw;
@@ -193,6 +204,7 @@ struct FusedArgs {
   int *mm_live;                   // [2] ordered-int min / max accumulated during the step
   unsigned long long *sync;       // [2] grid-barrier arrivals, completions (only ever grow)
   int *status;                    // KTUNE_ETIMEOUT when a barrier wait gave up
+  int *status_out;                // when set, the last CTA moves *status here and clears it
   uint64_t *cand;                 // [grid][KTUNE_MAX_K] per-CTA top-k keys
   uint32_t *list;                 // on-the-fly spaces: the step's one-word digits of TS by ordinal
   uint64_t wait_ns;               // limit of each barrier wait
@@ -569,9 +581,8 @@ struct ktune_search {
   int *d_nout = nullptr;
   // pinned host staging
   float *h_counters = nullptr;
-  int64_t *h_out_raw = nullptr;
-  float *h_out_score = nullptr;
-  uint64_t *h_out_packed = nullptr;
+  ktune::HostOut *hout = nullptr;       // ktune_step's outputs, mapped pinned host memory
+  ktune::HostOut *hout_dev = nullptr;   // the same block as the device addresses it
   int *h_nout = nullptr;
 };
 

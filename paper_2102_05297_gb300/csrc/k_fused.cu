@@ -433,13 +433,15 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
         __syncwarp();
       }
       const uint32_t *bw = buf + bsel * kSubTile;
-      // lane l: the sum of weights 32 l .. 32 l + 31, then a scan over the lanes
+      // lane l: the sum of weights 32 l .. 32 l + 31, then a scan over the
+      // lanes (the lanes start at different quarters of their 128 bytes, so
+      // that a load spreads over all banks)
       uint64_t ls = 0;
       {
         const uint4 *s4 = reinterpret_cast<const uint4 *>(bw + lane * 32);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const uint4 x = s4[q];
+          const uint4 x = s4[(q + lane) & 7];
           ls += (uint64_t)x.x + x.y + (uint64_t)x.z + x.w;
         }
       }
@@ -467,7 +469,7 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
         atomicOr(sd.eval + (i >> 5), 1u << (i & 31));
       }
       {
-        const int o = (int)(sp / per);   // the lane whose super-tile slice holds sp
+        const int o = (int)sp / (int)per;   // the lane whose super-tile slice holds sp
         if (lane == o) local -= wi;
         if (lane >= o) incl -= wi;
         W -= wi;
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   constexpr int kListBytes = NW * KTUNE_MAX_K * 8;
   __shared__ float sh_A[KTUNE_MAX_COUNTERS], sh_dl[KTUNE_MAX_COUNTERS];
   __shared__ int sh_active[KTUNE_MAX_COUNTERS];
-  __shared__ int sh_nact, sh_ok, sh_last;
+  __shared__ int sh_ncand, sh_nact, sh_ok, sh_last;
   __shared__ float red_mn[NW], red_mx[NW];
   __shared__ int sh_any[NW];
   const SearchDev &sd = fa.sd;
@@ -660,33 +662,57 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   for (int64_t off = (int64_t)threadIdx.x * 32; off < (hi - lo) / 32 + 1; off += (int64_t)THREADS * 32)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.eval + (lo >> 5) + off));
   // ---- P0: c_profile's prediction per counter, the active counters ----------------
-  // The node bytes of all K trees are copied into shared memory in one round
-  // trip when they fit, so that c_profile's walks do not wait on a chain of
-  // dependent global loads.
-  const bool staged = L >= 16 && (size_t)K * L <= (size_t)kFusedSmem;
+  // Only the counters with Delta_p != 0 (known before the step) can be
+  // active, so only their trees are walked for c_profile: their node bytes
+  // are copied into shared memory in one round trip when they fit, so that
+  // the walks do not wait on a chain of dependent global loads.  pc(c_profile)
+  // of the other counters is left 0 (nothing reads it).
+  if (warp == 0) {
+    int base = 0;
+    for (int q0 = 0; q0 < K; q0 += 32) {
+      const int q = q0 + lane;
+      const float dl = q < K ? st.delta[q] : 0.0f;
+      if (q < K) {
+        sh_dl[q] = dl;
+        sh_A[q] = 0.0f;
+      }
+      const unsigned m = __ballot_sync(kFullMask, dl != 0.0f);
+      if (dl != 0.0f) sh_active[base + __popc(m & ((1u << lane) - 1u))] = q;
+      base += __popc(m);
+    }
+    if (lane == 0) sh_ncand = base;
+  }
+  __syncthreads();
+  const int n_cand = sh_ncand;
+  const bool staged = L >= 16 && (size_t)n_cand * L <= (size_t)kFusedSmem;
   if (staged) {
-    const int n16 = (K * L) >> 4;
+    const int per16 = L >> 4, n16 = n_cand * per16;
     for (int i = threadIdx.x; i < n16; i += THREADS)
-      cp_async16(smem + 16 * i, sd.nodes + 16 * (size_t)i);
+      cp_async16(smem + 16 * (size_t)i, sd.nodes + (size_t)sh_active[i / per16] * L + 16 * (size_t)(i % per16));
     cp_async_wait_all();
     __syncthreads();
   }
   if (warp == 0) {
     const uint32_t plo = (uint32_t)st.cprof_packed, phi = (uint32_t)(st.cprof_packed >> 32);
-    for (int p = lane; p < K; p += 32) {
-      const uint8_t *nd = staged ? smem + (size_t)p * L : sd.nodes + (size_t)p * L;
+    for (int c = lane; c < n_cand; c += 32) {
+      const int p = sh_active[c];
+      const uint8_t *nd = staged ? smem + (size_t)c * L : sd.nodes + (size_t)p * L;
       uint32_t i = 0;
       for (int l = 0; l < D; ++l) i = tree_step(i, staged ? nd[i] : __ldg(nd + i), plo, phi);
       sh_A[p] = __ldg(sd.leaves + (size_t)p * L + (i - (uint32_t)(L - 1)));
-      sh_dl[p] = st.delta[p];
     }
     __syncwarp();
+    // the candidates with pc_p(c_profile) != 0, in counter order (in place:
+    // every lane reads its entry before any lane writes)
     int base = 0;
-    for (int q0 = 0; q0 < K; q0 += 32) {
-      const int q = q0 + lane;
-      const bool act = q < K && sh_dl[q] != 0.0f && sh_A[q] != 0.0f;
+    for (int c0 = 0; c0 < n_cand; c0 += 32) {
+      const int c = c0 + lane;
+      const int p = c < n_cand ? sh_active[c] : 0;
+      const bool act = c < n_cand && sh_A[p] != 0.0f;
       const unsigned m = __ballot_sync(kFullMask, act);
-      if (act) sh_active[base + __popc(m & ((1u << lane) - 1u))] = q;
+      __syncwarp();
+      if (act) sh_active[base + __popc(m & ((1u << lane) - 1u))] = p;
+      __syncwarp();
       base += __popc(m);
     }
     if (lane == 0) sh_nact = base;
@@ -872,6 +898,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   stamp(fa, 7, true);
   if (threadIdx.x == 0) {
     if (st.n_out) *st.n_out = count;
+    if (fa.status_out) *fa.status_out = atomicExch(fa.status, 0);
     sd.mm[0] = __ldcg(fa.mm_live);
     sd.mm[1] = __ldcg(fa.mm_live + 1);
     fa.mm_live[0] = INT_MAX;

@@ -270,8 +270,18 @@ class Search:
         self.k = k
         self.K = model.K
         self.space, self.model = space, model
+        self._buffers()
+
+    def _buffers(self):
+        """step()'s argument buffers, with their ctypes pointers made once."""
         self._raw = np.empty(64, np.int64)
         self._score = np.empty(64, np.float32)
+        self._cnt = np.empty(64, np.float32)
+        self._cnt_p = self._cnt.ctypes.data_as(_f32p)
+        self._raw_p = self._raw.ctypes.data_as(_i64p)
+        self._score_p = self._score.ctypes.data_as(_f32p)
+        self._n = C.c_int()
+        self._n_ref = C.byref(self._n)
 
     def current(self) -> int:
         r = C.c_int64()
@@ -285,13 +295,15 @@ class Search:
         """Returns (raw indices, scores); raises KtuneError except on
         KTUNE_EXHAUSTED, where the partial batch is returned."""
         k = self.k if k is None else k
-        c, cp = _arr(counters, np.float32)
-        n = C.c_int()
-        rc = lib.ktune_step(self.h, cp, k, self._raw.ctypes.data_as(C.POINTER(C.c_int64)),
-                            self._score.ctypes.data_as(C.POINTER(C.c_float)), C.byref(n))
+        c = np.asarray(counters, np.float32).reshape(-1)
+        if c.shape[0] < self.K:
+            raise ValueError("expected %d counters, got %d" % (self.K, c.shape[0]))
+        self._cnt[:self.K] = c[:self.K]
+        rc = lib.ktune_step(self.h, self._cnt_p, k, self._raw_p, self._score_p, self._n_ref)
         if rc not in (KTUNE_OK, KTUNE_EXHAUSTED):
             check(rc, "ktune_step")
-        return self._raw[:n.value].copy(), self._score[:n.value].copy()
+        n = self._n.value
+        return self._raw[:n].copy(), self._score[:n].copy()
 
     def step_device(self, counters, k: int, out_raw_ptr: int, out_score_ptr: int,
                     n_out_ptr: int = 0, stream=None):
@@ -360,8 +372,7 @@ class Search:
         self.k = hdr_k
         self.K = model.K
         self.space, self.model = space, model
-        self._raw = np.empty(64, np.int64)
-        self._score = np.empty(64, np.float32)
+        self._buffers()
         return self
 
     def close(self):
