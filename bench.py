@@ -68,7 +68,7 @@ WORKLOADS = {
     "mid_12p": dict(space="mid_12p", K=32, depth=12, frac=0.02, noise=0.02, k=5),
     "tiny_block_tile": dict(space=None, K=16, depth=8, frac=0.10, noise=0.0, k=5),
 }
-ALL_PATHS = ("chain", "mlp", "lsq", "cached", "table", "nbr", "batch", "large", "tiny")
+ALL_PATHS = ("chain", "mlp", "lsq", "cached", "table", "nbr", "batch", "large", "mlp_large", "tiny")
 # DRAM bytes (read + write) per launch of each path's dominant kernel, from the ncu
 # captures summarised under profiles/ (the kernels have not changed since)
 PROFILED_TRAFFIC = {
@@ -348,6 +348,8 @@ def run_ours(args):
             paths["batch"] = path_batch(ctx)
         if "large" in want:
             paths["large"] = path_large(ctx)
+        if "mlp_large" in want:
+            paths["mlp_large"] = path_mlp_large(ctx)
         if "tiny" in want:
             paths["tiny"] = path_tiny(ctx)
 
@@ -969,6 +971,129 @@ def path_large(ctx, depth=12):
                      "frac": ach / peak, "traffic": PROFILED_TRAFFIC.get("k_step_fused_otf"),
                      "mean_active_counters": float(np.mean(nact)),
                      "phase_share": {n: kern_ms[1 + i] / kern_ms[0] for i, n in enumerate(names) if n}},
+    }
+
+
+def path_mlp_large(ctx, n_fit=40000, k=16):
+    """The MLP on the large space (16 parameters, 19.5M valid configurations,
+    materialised here because the network reads packed digits), K = 40
+    counters, 16 weighted draws per step (MLP searches take weighted draws
+    only): GPU training, counter RMSE against depth-12 trees
+    fitted on the same profile sample, and the step time of both models on
+    the same recorded trajectory."""
+    kt, torch, stream, flush = ctx["kt"], ctx["torch"], ctx["stream"], ctx["flush"]
+    from paper_2102_05297_gb300 import fit
+    d = W.load_space("large_16p")
+    Kc = 40
+    roles = W.layout(Kc)
+    gpu = SyntheticGPU(d, roles, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sp = kt.Space.from_desc(d)
+    n = sp.count()[0]
+    create_s = time.perf_counter() - t0
+    valid = sp.valid_raw()
+    digits = sp.valid_digits()
+    samp = sample_indices(n, n_fit / n, 21)
+    Y = add_noise(gpu.evaluate(digits[samp])[0], 21, 0.02)
+    ranges = gpu.counter_ranges()
+    t0 = time.perf_counter()
+    tree_model = fit.fit_model(digits[samp], Y, 12, d.radices, roles)
+    fit_s = time.perf_counter() - t0
+    tm = kt.Model(sp, tree_model)
+    rest = np.setdiff1d(np.arange(n), samp)
+    held = np.sort(np.random.default_rng(22).choice(rest, size=max(1, n // 100), replace=False))
+    truth = gpu.evaluate(digits[held])[0].astype(np.float64)
+    # tree predictions of the held-out rows, by chunks of TS ordinals
+    chunk = 1 << 21
+    buf = torch.empty((chunk, Kc), dtype=torch.float32, device="cuda")
+    tree_pred = np.empty((len(held), Kc), np.float32)
+    for lo in range(0, n, chunk):
+        cnt = min(chunk, n - lo)
+        tm.predict_device(lo, cnt, buf.data_ptr(), stream)
+        sel = held[(held >= lo) & (held < lo + cnt)]
+        if len(sel):
+            rows = torch.from_numpy(sel - lo).cuda()
+            tree_pred[np.searchsorted(held, sel)] = buf[rows].cpu().numpy()
+    torch.cuda.synchronize()
+    del buf
+    rm_tree = rmse_norm(tree_pred, truth, ranges)
+
+    B, steps = 4096, ctx["mlp_train_steps"]
+    mlp = kt.Mlp(sp, roles, ranges, max_batch=B, stream=stream)
+    mlp.set_params(fit.init_mlp(mlp.F, Kc, seed=0))
+    mlp.set_data(valid[samp], Y)
+    idx = np.random.default_rng(23).integers(0, len(samp), size=steps * B).astype(np.int32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = mlp.train(idx, B)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    rm_mlp = rmse_norm(mlp.predict(valid[held]), truth, ranges)
+
+    # a trajectory recorded with the trees (c_profile, its counters, the batch runtimes)
+    Wu = ctx["warmup"]
+    n_steps = min(ctx["steps"], 20)
+    rec = kt.Search(sp, tm, k=k, seed=0)
+    traj = []
+    for _ in range(Wu + n_steps):
+        cp = rec.current()
+        pos = int(np.searchsorted(valid, cp))
+        c = gpu.evaluate(digits[pos:pos + 1])[0][0]
+        raw, _ = rec.step(c)
+        rec.report(gpu.evaluate(digits[np.searchsorted(valid, raw)])[1])
+        traj.append((cp, c))
+    rec.close()
+    bufs = (torch.empty(k, dtype=torch.int64, device="cuda").data_ptr(),
+            torch.empty(k, dtype=torch.float32, device="cuda").data_ptr(),
+            torch.empty(1, dtype=torch.int32, device="cuda").data_ptr())
+
+    def timed(model, timing):
+        s = kt.Search(sp, model, k=k, seed=0, stream=stream)
+        s.set_timing(timing)
+        untimed_device_steps(s, traj, 0, Wu, k, bufs, stream)
+        torch.cuda.synchronize()
+        out = timed_device_steps(kt, torch, s, traj, Wu, Wu + n_steps, k, stream, flush)
+        s.close()
+        return out
+
+    t_step, _, _, t_scored, _ = timed(tm, False)
+    model = kt.Model.from_mlp(mlp)
+    _, kern_ms, _, _, _ = timed(model, True)
+    m_step, _, _, m_scored, _ = timed(model, False)
+    model.close()
+    tm.close()
+    mlp.close()
+    sp.close()
+    tree_ms = sum(t_step) / len(t_step)
+    mlp_ms = sum(m_step) / len(m_step)
+    fpc = mlp_flops_per_config(mlp.F, Kc)
+    pk = ctx["pk"]
+    peak = float(pk.get("bf16_tflops", 1933.0)) * 1e12
+    ach = m_scored * fpc / (kern_ms[1] / 1e3)
+    return {
+        "workload": "MLP %d->256->256->256->%d on the large_16p space materialised (%d valid of %d "
+                    "raw, created in %.2f s), %d weighted draws per step; trees (depth 12) and MLP (Adam, %d "
+                    "steps x %d rows) fitted on the same %d-configuration profile sample + 2%% "
+                    "noise (trees fitted on the host in %.1f s)" % (
+                        mlp.F, Kc, n, d.n_raw, create_s, k, steps, B, len(samp), fit_s),
+        "value": m_scored / (sum(m_step) / 1e3), "unit": "configs/s", "ms_per_step": mlp_ms,
+        "steps": len(m_step),
+        "tree": {"value": t_scored / (sum(t_step) / 1e3), "unit": "configs/s", "ms_per_step": tree_ms},
+        "counter_rmse": {"mlp": rm_mlp, "tree": rm_tree,
+                         "definition": "range-normalised RMSE over all %d counters on a 1%% held-out "
+                                       "sample (%d configurations) against the noise-free synthetic "
+                                       "counters" % (Kc, len(held))},
+        "speedup_vs_tree": tree_ms / mlp_ms,
+        "train": {"ms": train_ms, "final_loss": float(losses[-1]), "first_loss": float(losses[0]),
+                  "tflops": 3.0 * fpc * B * steps / (train_ms / 1e3) / 1e12},
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_fwd<score> (fused forward + Eq. score)",
+                     "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": None,
+                     "peak_source": "%s bf16 burst (cuBLAS GEMM)" % ctx["src"],
+                     "flop_per_config": fpc},
     }
 
 

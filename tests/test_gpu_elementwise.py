@@ -150,6 +150,27 @@ def test_every_score_and_weight_stream_path(kt, fused):
     run(kt, d, model, steps=4, k=7, seed=2, stream=torch.cuda.Stream(), fseed=3, fused=fused)
 
 
+@pytest.fixture(scope="module")
+def flat_trees():
+    values = [list(range(8))] * 6 + [list(range(5)), list(range(4))]
+    d = W.SpaceDesc("flat_8p", ["p%d" % j for j in range(8)], values, [])
+    model = random_model(d.radices, W.layout(16), depth=8, seed=51)
+    valid = ospace.enumerate_valid(d)
+    pred = otrees.predict(model, ospace.decode(d.radices, valid))
+    return d, model, valid, pred
+
+
+@pytest.mark.parametrize("fused", [2, 0])
+def test_every_score_and_weight_beyond_shared_tile_sums(kt, flat_trees, fused):
+    """5.24M configurations (no constraints): more sub-tiles than the fused
+    step's draws keep in shared memory, so their super-tile sums are added up
+    while the weights are computed and the draws read sub-tile sums from
+    global memory."""
+    d, model, valid, pred = flat_trees
+    assert d.n_raw == 5242880 and d.n_raw // 1024 > 4096
+    run(kt, d, model, steps=3, k=9, seed=4, fseed=2, fused=fused, valid=valid, pred=pred)
+
+
 def test_every_score_and_weight_tiny_fitted(kt):
     d = W.space_tiny_block_tile()
     roles = W.layout(16)
