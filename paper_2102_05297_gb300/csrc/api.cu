@@ -533,6 +533,19 @@ int ktune_space_create(const ktune_space_desc *d, int flags, void *stream, ktune
       set_error("tile offsets copy failed");
       return cleanup(KTUNE_ECUDA);
     }
+    // the tiles that hold a valid configuration: the on-the-fly decode deals
+    // them to the warps in turn and never visits the others
+    std::vector<int32_t> ne;
+    for (int64_t t = 0; t < s->n_tiles; ++t)
+      if (s->tile_offset[t + 1] > s->tile_offset[t]) ne.push_back((int32_t)t);
+    s->n_ne_tiles = (int64_t)ne.size();
+    if (!ne.empty()) {
+      if ((rc = dalloc(&s->d_ne_tiles, ne.size()))) return cleanup(rc);
+      if (cudaMemcpy(s->d_ne_tiles, ne.data(), ne.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("tile list upload failed");
+        return cleanup(KTUNE_ECUDA);
+      }
+    }
   }
   if (flags == KTUNE_MATERIALISE) {
     if ((rc = dalloc(&s->d_packed, s->n_valid))) return cleanup(rc);
@@ -564,6 +577,7 @@ int ktune_space_destroy(ktune_space *s) {
   cudaFree(s->d_win_table);
   cudaFree(s->d_ci_table);
   cudaFree(s->d_tile_offset);
+  cudaFree(s->d_ne_tiles);
   delete s;
   return KTUNE_OK;
 }
@@ -980,6 +994,8 @@ int ktune_search_create(ktune_space *s, ktune_model *m, const ktune_search_opts 
   sd.packed = s->d_packed;
   sd.narrow = s->d_narrow;
   sd.tile_offset = s->d_tile_offset;
+  sd.ne_tiles = s->d_ne_tiles;
+  sd.n_ne_tiles = s->n_ne_tiles;
   sd.groups = s->d_groups;
   sd.table = s->d_table;
   sd.N = N;

@@ -127,6 +127,8 @@ struct SearchDev {
   const uint64_t *packed;     // materialised TS, nibble layout (or null)
   const uint32_t *narrow;     // materialised TS, one-word layout (or null)
   const int64_t *tile_offset; // valid prefix per raw tile of kEnumTileRaw (on-the-fly)
+  const int32_t *ne_tiles;    // the raw tiles holding a valid configuration, ascending (on-the-fly)
+  int64_t n_ne_tiles;
   const GroupDev *groups;
   const uint32_t *table;
   int64_t N;                  // valid configurations
@@ -438,6 +440,8 @@ struct ktune_space {
   uint8_t pos[KTUNE_MAX_PARAMS] = {0}, width[KTUNE_MAX_PARAMS] = {0};
   uint32_t *d_narrow = nullptr;      // TS in the narrow layout (materialised, narrow spaces)
   int64_t *d_tile_offset = nullptr;  // exclusive valid prefix per raw tile (+ total)
+  int32_t *d_ne_tiles = nullptr;     // tiles with at least one valid configuration (on-the-fly)
+  int64_t n_ne_tiles = 0;
   std::vector<int64_t> tile_offset;  // host copy (on-the-fly spaces)
   // window tables of the one-word layout (narrow spaces)
   std::vector<ktune::WinDev> win;

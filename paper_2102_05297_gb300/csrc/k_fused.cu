@@ -491,10 +491,12 @@ __device__ __forceinline__ uint64_t packed_of_word(const SearchDev &sd, uint32_t
   return p;
 }
 
-// PD of the fused step over an on-the-fly space: every CTA decodes its range
-// of raw tiles (4096 raw indices each; a warp takes whole tiles, a lane four
-// consecutive indices of each round of 128, by odometer steps), checks the
-// constraints, and writes the one-word digits of every valid configuration
+// PD of the fused step over an on-the-fly space: the grid's warps take the
+// raw tiles (4096 raw indices each) that hold a valid configuration in turn
+// (the list is made when the space is created; the tiles without one are
+// never visited) and decode them (a lane takes four consecutive indices of
+// each round of 128), check the
+// constraints, and write the one-word digits of every valid configuration
 // at its ordinal in fa.list (the tile's valid prefix plus its rank, counted
 // with warp scans).  TS is thus rebuilt in every step, never kept.
 __device__ __noinline__ void fused_decode(const FusedArgs &fa) {
@@ -531,13 +533,111 @@ __device__ __noinline__ void fused_decode(const FusedArgs &fa) {
     for (int i = threadIdx.x; i < sd.win_words; i += blockDim.x) tab[i] = __ldg(sd.win_table + i);
   __syncthreads();
   const uint32_t n_raw = (uint32_t)sd.sa.n_raw;
-  const int64_t n_tiles = (sd.sa.n_raw + kEnumTileRaw - 1) / kEnumTileRaw;
-  const int64_t t_lo = n_tiles * blockIdx.x / gridDim.x, t_hi = n_tiles * (blockIdx.x + 1) / gridDim.x;
+  // the tiles with a valid configuration, dealt to the grid's warps in turn
+  // (they cluster in the raw order; dealing them keeps the warps even)
+  const int64_t g0 = (int64_t)blockIdx.x * NW + warp, gstride = (int64_t)gridDim.x * NW;
+  const int64_t n_ne = sd.n_ne_tiles;
   const bool use_ci = ctx->ci_words > 0;
+  const int64_t N = sd.N;
   uint32_t *__restrict__ list = fa.list;
-  for (int64_t t = t_lo + warp; t < t_hi; t += NW) {
-    const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
+  // The low block: the fastest parameters whose radices are powers of two,
+  // as many as fit 12 bits (parameters jl .. P-1, wl bits).  Within a block
+  // of 2^wl consecutive raw indices (at a multiple of 2^wl) a raw index's
+  // digits of these parameters are its low wl bits, field by field, and the
+  // other digits are fixed.  With wl >= 7 a round of 128 raw indices (at a
+  // multiple of 128) lies in one block: a raw index's word is the high
+  // parameters' word OR the placement of its position in the block (the
+  // round's part, a shuffle from the lane that placed it, plus the lane's
+  // own offset o < 128, placed once); its constrained index adds up the same
+  // way.  Only the high parameters step an odometer, once per block.
+  int wl = 0, jl = ctx->P;
+  while (jl > 0) {
+    const int j = jl - 1;
+    if ((uint32_t)ctx->radix[j] != (1u << ctx->width[j]) || wl + ctx->width[j] > 12) break;
+    wl += ctx->width[j];
+    jl = j;
+  }
+  if (wl >= 7) {
+    auto place = [&](uint32_t v, uint32_t &word, uint32_t &ci) {
+      word = 0u;
+      ci = 0u;
+      for (int j = ctx->P - 1; j >= jl; --j) {
+        const uint32_t w = ctx->width[j], d = v & ((1u << w) - 1u);
+        word |= d << ctx->pos[j];
+        ci += d * ctx->cis[j];
+        v >>= w;
+      }
+    };
+    uint32_t lw[4], lc[4], pq, cq;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) place(4u * (uint32_t)lane + (uint32_t)u, lw[u], lc[u]);
+    place((uint32_t)(lane << 7) & ((1u << wl) - 1u), pq, cq);
+    const uint32_t qmask = (1u << (wl - 7)) - 1u;
+    for (int64_t e = g0; e < n_ne; e += gstride) {
+      const int64_t t = __ldg(sd.ne_tiles + e);
+      int64_t ord = __ldg(sd.tile_offset + t);
+      const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
+      // the high parameters' digits of the tile's first block
+      uint32_t h = tbase >> wl, Wh = 0u, xh = 0u;
+      for (int j = jl - 1; j >= 0; --j) {
+        const uint32_t r = ctx->radix[j], qt = h / r, d = h - qt * r;
+        Wh |= d << ctx->pos[j];
+        xh += d * ctx->cis[j];
+        h = qt;
+      }
+      for (int q = 0; q < kEnumTileRaw / 128; ++q) {
+        const uint32_t rb = tbase + (uint32_t)q * 128u;
+        if (rb >= n_raw) break;                       // warp-uniform
+        const uint32_t qlo = (rb >> 7) & qmask;
+        if (q > 0 && qlo == 0) {                      // the next block: one odometer step
+          for (int j = jl - 1; j >= 0; --j) {
+            const uint32_t sh = ctx->pos[j], m = (1u << ctx->width[j]) - 1u;
+            const uint32_t d = ((Wh >> sh) & m) + 1u;
+            if (d < ctx->radix[j]) {
+              Wh += 1u << sh;
+              xh += ctx->cis[j];
+              break;
+            }
+            xh -= (d - 1u) * ctx->cis[j];
+            Wh &= ~(m << sh);
+          }
+        }
+        const uint32_t Wr = Wh | __shfl_sync(kFullMask, pq, qlo);
+        const uint32_t xr = xh + __shfl_sync(kFullMask, cq, qlo);
+        const uint32_t r0 = rb + 4u * (uint32_t)lane;
+        const int n_here = r0 >= n_raw ? 0 : (int)min(4u, n_raw - r0);
+        uint32_t Wq[4];
+        uint32_t vm = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Wq[u] = Wr | lw[u];
+        if (use_ci) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t x = xr + lc[u];
+            if (u < n_here && ((tab[x >> 5] >> (x & 31)) & 1u)) vm |= 1u << u;
+          }
+        } else {
+          vm = otf_valid4(ctx, sd, Wq, n_here);
+        }
+        const uint32_t cnt = __popc(vm);
+        const uint32_t incl = warp_incl(cnt);
+        const uint32_t tot = __shfl_sync(kFullMask, incl, 31);
+        int64_t at = ord + (incl - cnt);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((vm >> u) & 1u) {
+            if (at < N) list[at] = Wq[u];   // (always: the tile's valid prefix counts the same bits)
+            ++at;
+          }
+        ord += tot;
+      }
+    }
+    return;
+  }
+  for (int64_t e = g0; e < n_ne; e += gstride) {
+    const int64_t t = __ldg(sd.ne_tiles + e);
     int64_t ord = __ldg(sd.tile_offset + t);
+    const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
     uint32_t W = otf_decode(ctx, tbase + 4u * (uint32_t)lane);
     uint32_t xci = use_ci ? otf_ci(ctx, W) : 0u;
     for (int q = 0; q < kEnumTileRaw / 128; ++q) {
@@ -547,15 +647,16 @@ __device__ __noinline__ void fused_decode(const FusedArgs &fa) {
       const int n_here = r0 >= n_raw ? 0 : (int)min(4u, n_raw - r0);
       uint32_t Wq[4];
       uint32_t vm = 0;
-      Wq[0] = W;
       if (use_ci) {
         uint32_t x = xci;
+        Wq[0] = W;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (u > 0) Wq[u] = otf_next_ci(ctx, Wq[u - 1], x);
           if (u < n_here && ((tab[x >> 5] >> (x & 31)) & 1u)) vm |= 1u << u;
         }
       } else {
+        Wq[0] = W;
 #pragma unroll
         for (int u = 1; u < 4; ++u) Wq[u] = otf_next(ctx, Wq[u - 1]);
         vm = otf_valid4(ctx, sd, Wq, n_here);
@@ -563,10 +664,13 @@ __device__ __noinline__ void fused_decode(const FusedArgs &fa) {
       const uint32_t cnt = __popc(vm);
       const uint32_t incl = warp_incl(cnt);
       const uint32_t tot = __shfl_sync(kFullMask, incl, 31);
-      uint32_t slot = incl - cnt;
+      int64_t at = ord + (incl - cnt);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if ((vm >> u) & 1u) list[ord + slot++] = Wq[u];
+        if ((vm >> u) & 1u) {
+          if (at < N) list[at] = Wq[u];   // (always: the tile's valid prefix counts the same bits)
+          ++at;
+        }
       ord += tot;
       W = otf_add128(ctx, W, xci);
     }
