@@ -46,7 +46,8 @@ extern __shared__ __align__(16) uint8_t fz_smem[];
 constexpr int kSpec = 16;                // draws whose sub-tile is fetched ahead
 constexpr int kF3Super = kMaxSuper;      // P3: super-tile sums in shared memory
 constexpr int kF3Sub = 4096;             // P3: sub-tile sums kept in shared memory when they fit
-static_assert(kF3Super * 8 + kF3Sub * 8 + (kSpec + 1) * kSubTile * 4 <= kFusedSmem, "P3 layout");
+static_assert(kF3Super * 8 + kF3Sub * 8 + (kSpec + 1) * 32 * 8 + (kSpec + 1) * kSubTile * 4 <= kFusedSmem,
+              "P3 layout");
 
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
@@ -268,6 +269,19 @@ __device__ __noinline__ void fused_weights(const FusedArgs &fa) {
 // P3 of the fused step in sample mode, by the CTA that finishes last: the k
 // draws without replacement of Algorithm 1; returns how many were made (fewer
 // than k once every remaining weight is 0) with their ordinals in pick[].
+//
+// A draw value r, uniform in [0, W) for the remaining total W, is located in
+// three levels: the super-tile (each lane keeps a slice of the super-tile
+// sums and their running total), the sub-tile (inclusive prefix sums of the
+// sub-tile sums within each super-tile, in shared memory when they fit: one
+// ballot; else read and scanned), and the configuration (inclusive prefix
+// sums of the sub-tile's 32 groups of 32 weights: one ballot, then the
+// group's weights scanned).  The sub-tiles of the first kSpec draws, as they
+// would fall without the earlier draws' removals, are fetched in parallel
+// first, each with its group prefixes; another sub-tile is fetched when a
+// draw lands in it.  Fetched weights are those before this step's draws: an
+// earlier pick's weight is taken off where a draw reads it, and the picks'
+// weights are zeroed in global memory after the last draw.
 // Out of line, so that its registers do not count against the walk's.
 __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   const SearchDev &sd = fa.sd;
@@ -278,25 +292,22 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   const int k = st.k;
   uint8_t *smem = fz_smem;
   __shared__ int sh_n;
-  // k draws without replacement: super-tile -> sub-tile -> configuration,
-  // each a warp scan.  The sub-tiles of the first kSpec draws, as they
-  // would fall without the earlier draws' removals, are fetched in parallel
-  // first; a draw that lands in a fetched sub-tile reads its weights from
-  // shared memory (a draw zeroes its weight there too).
+  __shared__ uint32_t pick_w[KTUNE_MAX_K];   // the picks' weights
+  __shared__ int64_t spec_g[kSpec];          // the sub-tile fetched into buffer b (-1: none)
   const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
   const int64_t n_super = (n_sub + kSuper - 1) / kSuper;
-  uint64_t *sup = reinterpret_cast<uint64_t *>(smem);
-  uint64_t *subc = sup + kF3Super;
-  uint32_t *buf = reinterpret_cast<uint32_t *>(subc + kF3Sub);
-  __shared__ int64_t spec_g[kSpec];
+  uint64_t *sup = reinterpret_cast<uint64_t *>(smem);   // super-tile sums
+  uint64_t *subp = sup + kF3Super;                      // sub-tile prefix sums per super-tile (cached)
+  uint64_t *gp = subp + kF3Sub;                         // [kSpec + 1][32] group prefix sums of the buffers
+  uint32_t *buf = reinterpret_cast<uint32_t *>(gp + (kSpec + 1) * 32);   // [kSpec + 1][kSubTile] weights
   const bool cached = n_sub <= kF3Sub;
   // the tile sums, every copy in flight before one wait (pairs of sums per
   // copy); with the sub-tile sums in shared memory the super-tile sums are
   // their sums, else they were accumulated with the weights
   if (cached) {
     for (int64_t i = threadIdx.x; 2 * i < n_sub; i += THREADS) {
-      if (2 * i + 1 < n_sub) cp_async16(subc + 2 * i, sd.sub_sum + 2 * i);
-      else subc[2 * i] = __ldcg(sd.sub_sum + 2 * i);
+      if (2 * i + 1 < n_sub) cp_async16(subp + 2 * i, sd.sub_sum + 2 * i);
+      else subp[2 * i] = __ldcg(sd.sub_sum + 2 * i);
     }
   } else {
     for (int64_t i = threadIdx.x; 2 * i < n_super; i += THREADS) {
@@ -307,13 +318,17 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   if (threadIdx.x < kSpec) spec_g[threadIdx.x] = -1;
   cp_async_wait_all();
   __syncthreads();
-  if (cached) {
-    for (int64_t sp = threadIdx.x; sp < n_super; sp += THREADS) {
-      uint64_t t = 0;
-      const int64_t g1 = min(n_sub, (sp + 1) * kSuper);
-      for (int64_t g = sp * kSuper; g < g1; ++g) t += subc[g];
-      sup[sp] = t;
-      sd.super_sum[sp] = t;      // for inspection; the draws use the shared copy
+  if (cached) {   // prefix sums in place: a warp per super-tile, one sub-tile per lane
+    const int NW = THREADS >> 5;
+    for (int64_t sp = warp; sp < n_super; sp += NW) {
+      const int64_t gi = sp * kSuper + lane;
+      const uint64_t v = gi < n_sub ? subp[gi] : 0ull;
+      const uint64_t t = warp_incl(v);
+      if (gi < n_sub) subp[gi] = t;
+      if (lane == 31) {
+        sup[sp] = t;
+        sd.super_sum[sp] = t;    // for inspection; the draws use the shared copy
+      }
     }
     __syncthreads();
   }
@@ -322,9 +337,10 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   const uint32_t sid = sd.search_id, stp = st.step;
   const int64_t per = (n_super + 31) / 32;
   const int64_t slo = min(n_super, per * lane), shi = min(n_super, slo + per);
-  // locate draw value r: super-tile sp, sub-tile g and the remainder r2
-  // within it (called by a whole warp; false if the sums are inconsistent)
-  auto locate = [&](uint64_t r, uint64_t local, uint64_t incl, int64_t &sp_o, int64_t &g_o,
+  // locate draw value r: super-tile sp, sub-tile g (gl within sp), its
+  // remaining sum vg and the remainder r2 within it (called by a whole warp;
+  // false if the sums are inconsistent)
+  auto locate = [&](uint64_t r, uint64_t local, uint64_t incl, int64_t &sp_o, int64_t &g_o, int &gl_o,
                     uint64_t &vg_o, uint64_t &r2_o) -> bool {
     int64_t sp_sel = -1;
     uint64_t r1 = 0;
@@ -343,14 +359,29 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
     if (src1 < 0) return false;
     sp_sel = __shfl_sync(kFullMask, sp_sel, src1);
     r1 = __shfl_sync(kFullMask, r1, src1);
-    const int64_t gl = sp_sel * kSuper + lane;
-    const uint64_t v = gl < n_sub ? (cached ? subc[gl] : __ldcg(sd.sub_sum + gl)) : 0ull;
-    const uint64_t inc = warp_incl(v);
-    const int src2 = __ffs(__ballot_sync(kFullMask, inc - v <= r1 && r1 < inc)) - 1;
-    if (src2 < 0) return false;
-    g_o = __shfl_sync(kFullMask, gl, src2);
-    vg_o = __shfl_sync(kFullMask, v, src2);
-    r2_o = r1 - __shfl_sync(kFullMask, inc - v, src2);
+    const int64_t gi = sp_sel * kSuper + lane;
+    if (cached) {
+      const uint64_t pv = gi < n_sub ? subp[gi] : ~0ull;
+      const unsigned over = __ballot_sync(kFullMask, pv > r1);
+      if (!over) return false;
+      const int gl = __ffs(over) - 1;
+      const uint64_t pg = __shfl_sync(kFullMask, pv, gl);
+      const uint64_t pb = __shfl_sync(kFullMask, pv, gl > 0 ? gl - 1 : 0);
+      const uint64_t base = gl > 0 ? pb : 0ull;
+      g_o = sp_sel * kSuper + gl;
+      gl_o = gl;
+      vg_o = pg - base;
+      r2_o = r1 - base;
+    } else {
+      const uint64_t v = gi < n_sub ? __ldcg(sd.sub_sum + gi) : 0ull;
+      const uint64_t inc = warp_incl(v);
+      const int src2 = __ffs(__ballot_sync(kFullMask, inc - v <= r1 && r1 < inc)) - 1;
+      if (src2 < 0) return false;
+      g_o = __shfl_sync(kFullMask, gi, src2);
+      gl_o = src2;
+      vg_o = __shfl_sync(kFullMask, v, src2);
+      r2_o = r1 - __shfl_sync(kFullMask, inc - v, src2);
+    }
     sp_o = sp_sel;
     return g_o >= 0 && g_o < n_sub;
   };
@@ -360,6 +391,38 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
     incl = warp_incl(local);
     return __shfl_sync(kFullMask, incl, 31);
   };
+  // sub-tile g's weights into buffer b, every copy in flight at once (a warp)
+  auto fetch = [&](int b, int64_t g) {
+    const int64_t i0 = g * kSubTile;
+    uint32_t *d = buf + b * kSubTile;
+    for (int q = lane; q < kSubTile / 4; q += 32) {
+      const int64_t i = i0 + 4 * q;
+      if (i + 3 < N) {
+        cp_async16(d + 4 * q, sd.w + i);
+      } else {
+        uint4 x;
+        x.x = i < N ? __ldcg(sd.w + i) : 0u;
+        x.y = i + 1 < N ? __ldcg(sd.w + i + 1) : 0u;
+        x.z = i + 2 < N ? __ldcg(sd.w + i + 2) : 0u;
+        x.w = 0u;
+        reinterpret_cast<uint4 *>(d)[q] = x;
+      }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    // lane l: the sum of weights 32 l .. 32 l + 31 (the lanes start at
+    // different quarters of their 128 bytes, so that a load spreads over all
+    // banks), then the inclusive prefix over the groups
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(d + lane * 32);
+    uint64_t ls = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint4 x = s4[(q + lane) & 7];
+      ls += (uint64_t)x.x + x.y + (uint64_t)x.z + x.w;
+    }
+    gp[b * 32 + lane] = warp_incl(ls);
+    __syncwarp();
+  };
   // speculative fetch: warp w takes draw w
   if (warp < min(k, kSpec)) {
     uint64_t local, incl;
@@ -367,35 +430,22 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
     if (W > 0) {
       const uint64_t r = scaled_draw(philox_u64(seed, sid, stp, (uint32_t)warp, 0u), W);
       int64_t sp, g;
+      int gl;
       uint64_t vg, r2;
-      if (locate(r, local, incl, sp, g, vg, r2)) {
-        const int64_t i0 = g * kSubTile;
-        uint32_t *b = buf + warp * kSubTile;
-        for (int q = lane; q < kSubTile / 4; q += 32) {   // all copies in flight at once
-          const int64_t i = i0 + 4 * q;
-          if (i + 3 < N) {
-            cp_async16(b + 4 * q, sd.w + i);
-          } else {
-            uint4 x;
-            x.x = i < N ? __ldcg(sd.w + i) : 0u;
-            x.y = i + 1 < N ? __ldcg(sd.w + i + 1) : 0u;
-            x.z = i + 2 < N ? __ldcg(sd.w + i + 2) : 0u;
-            x.w = 0u;
-            reinterpret_cast<uint4 *>(b)[q] = x;
-          }
-        }
+      if (locate(r, local, incl, sp, g, gl, vg, r2)) {
+        fetch(warp, g);
         if (lane == 0) spec_g[warp] = g;
       }
     }
   }
-  cp_async_wait_all();
   __syncthreads();
   if (warp == 0) {
-    uint32_t *__restrict__ wp = sd.w;
-    const int64_t my_spec = lane < kSpec ? spec_g[lane] : -1;   // the sub-tile fetched into buffer lane
+    // (ordinals and sub-tile indices fit 32 bits: at most kMaxSuper super-tiles)
+    const int my_spec = lane < kSpec ? (int)spec_g[lane] : -1;   // the sub-tile fetched into buffer lane
     const uint64_t u_lo = philox_u64(seed, sid, stp, (uint32_t)lane, 0u);
     const uint64_t u_hi = lane + 32 < k ? philox_u64(seed, sid, stp, (uint32_t)(lane + 32), 0u) : 0ull;
     int count = 0;
+    int my_pick = -1;   // lane q < 32: pick q
     // the super-tile totals once; each pick then lowers them where it lies
     uint64_t local, incl;
     uint64_t W = totals(local, incl);
@@ -404,67 +454,56 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
       const uint64_t uj = j < 32 ? __shfl_sync(kFullMask, u_lo, j) : __shfl_sync(kFullMask, u_hi, j - 32);
       const uint64_t r = scaled_draw(uj, W);
       int64_t sp, g;
+      int gl;
       uint64_t vg, r2;
-      if (!locate(r, local, incl, sp, g, vg, r2)) break;   // cannot happen with consistent sums
-      // the sub-tile's weights in shared memory: a fetched copy, else copied
-      // now into the scratch buffer kSpec (earlier draws zeroed theirs in L2)
-      const unsigned has = __ballot_sync(kFullMask, my_spec == g);
-      int bsel = has ? __ffs(has) - 1 : kSpec;
-      if (bsel == kSpec) {
-        uint32_t *b = buf + kSpec * kSubTile;
-        for (int q = lane; q < kSubTile / 4; q += 32) {
-          const int64_t i = g * kSubTile + 4 * q;
-          if (i + 3 < N) {
-            cp_async16(b + 4 * q, wp + i);
-          } else {
-            uint4 x;
-            x.x = i < N ? __ldcg(wp + i) : 0u;
-            x.y = i + 1 < N ? __ldcg(wp + i + 1) : 0u;
-            x.z = i + 2 < N ? __ldcg(wp + i + 2) : 0u;
-            x.w = 0u;
-            reinterpret_cast<uint4 *>(b)[q] = x;
-          }
+      if (!locate(r, local, incl, sp, g, gl, vg, r2)) break;   // cannot happen with consistent sums
+      const unsigned has = __ballot_sync(kFullMask, (int64_t)my_spec == g);
+      const int bsel = has ? __ffs(has) - 1 : kSpec;
+      if (bsel == kSpec) fetch(kSpec, g);
+      // the group: the group prefix sums less the earlier picks' weights in
+      // this sub-tile up to the group (lane q < count holds pick q)
+      const bool here = lane < count && (int64_t)(my_pick / kSubTile) == g;
+      const bool any_here = __any_sync(kFullMask, here) || count > 32;
+      uint64_t adj = 0;
+      if (any_here)
+        for (int q = 0; q < count; ++q) {
+          const int64_t o = pick[q] - g * kSubTile;
+          if (o >= 0 && o < kSubTile && (int)(o >> 5) <= lane) adj += pick_w[q];
         }
-        cp_async_wait_all();
-        __syncwarp();
-        // the earlier picks in this sub-tile read 0 whatever the copy saw
-        for (int q = lane; q < count; q += 32)
-          if (pick[q] / kSubTile == g) b[pick[q] - g * kSubTile] = 0u;
-        __syncwarp();
+      const uint64_t gpa = gp[bsel * 32 + lane] - adj;
+      const unsigned over = __ballot_sync(kFullMask, gpa > r2);
+      if (!over) break;                // cannot happen with consistent sums
+      const int og = __ffs(over) - 1;
+      const uint64_t gprev = __shfl_sync(kFullMask, gpa, og > 0 ? og - 1 : 0);
+      const uint64_t r3 = r2 - (og > 0 ? gprev : 0ull);
+      // the group's weights, one per lane (the earlier picks' read 0), scanned
+      const int64_t ii = g * kSubTile + og * 32 + lane;
+      uint32_t wq = buf[bsel * kSubTile + og * 32 + lane];
+      if (any_here)
+        for (int q = 0; q < count; ++q)
+          if (pick[q] == ii) wq = 0u;
+      // a group's 32 weights (each < 2^29) sum below 2^32 but in rare cases:
+      // a 32-bit scan then, else a 64-bit one
+      const uint64_t gsum = __shfl_sync(kFullMask, gpa, og) - (og > 0 ? gprev : 0ull);
+      unsigned hit;
+      if (gsum < (1ull << 32)) {
+        const uint32_t iq = warp_incl(wq);
+        hit = __ballot_sync(kFullMask, (uint64_t)(iq - wq) <= r3 && r3 < (uint64_t)iq);
+      } else {
+        const uint64_t iq = warp_incl((uint64_t)wq);
+        hit = __ballot_sync(kFullMask, iq - wq <= r3 && r3 < iq);
       }
-      const uint32_t *bw = buf + bsel * kSubTile;
-      // lane l: the sum of weights 32 l .. 32 l + 31, then a scan over the
-      // lanes (the lanes start at different quarters of their 128 bytes, so
-      // that a load spreads over all banks)
-      uint64_t ls = 0;
-      {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(bw + lane * 32);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint4 x = s4[(q + lane) & 7];
-          ls += (uint64_t)x.x + x.y + (uint64_t)x.z + x.w;
-        }
-      }
-      const uint64_t inc3 = warp_incl(ls);
-      const unsigned own = __ballot_sync(kFullMask, inc3 - ls <= r2 && r2 < inc3);
-      if (!own) break;                 // cannot happen with consistent sums
-      // the lane holding r2; its 32 weights, one per lane, scanned by the warp
-      const int ol = __ffs(own) - 1;
-      const uint64_t rr = r2 - __shfl_sync(kFullMask, inc3 - ls, ol);
-      const uint32_t wq = bw[ol * 32 + lane];
-      const uint64_t iq = warp_incl((uint64_t)wq);
-      const unsigned hit = __ballot_sync(kFullMask, iq - wq <= rr && rr < iq);
-      if (!hit) break;
+      if (!hit) break;                 // cannot happen with consistent sums
       const int qs = __ffs(hit) - 1;
-      const int64_t i = g * kSubTile + ol * 32 + qs;
+      const int64_t i = g * kSubTile + og * 32 + qs;
       const uint32_t wi = __shfl_sync(kFullMask, wq, qs);
-      // the pick's weight becomes 0 everywhere it is kept
-      if (my_spec == g) buf[lane * kSubTile + (i - g * kSubTile)] = 0u;
+      // the pick's weight comes off the sums that hold it
+      if (cached && lane >= gl && sp * kSuper + lane < n_sub) subp[sp * kSuper + lane] -= wi;
+      if (lane == j) my_pick = (int)i;
       if (lane == 0) {
         pick[j] = i;
-        wp[i] = 0;
-        if (cached) subc[g] = vg - wi;
-        else sd.sub_sum[g] = vg - wi;
+        pick_w[j] = wi;
+        if (!cached) sd.sub_sum[g] = vg - wi;
         sup[sp] -= wi;
         atomicOr(sd.eval + (i >> 5), 1u << (i & 31));
       }
@@ -477,6 +516,8 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
       __syncwarp();
       ++count;
     }
+    // the picks' weights read 0 from now on
+    for (int q = lane; q < count; q += 32) sd.w[pick[q]] = 0u;
     if (lane == 0) sh_n = count;
   }
   __syncthreads();
