@@ -16,7 +16,7 @@
 //               over the unevaluated ones.
 // The MMAs of one tile overlap the epilogue of the other.  Roundings: the
 // products accumulate in FP32 in tensor memory; bias, GELU (its erf from a
-// published rational approximation, gelu_p) and the output scale in FP32;
+// published rational approximation, gelu2_bf) and the output scale in FP32;
 // activations rounded to bfloat16; the score sums its counters in ascending
 // order, each term one float32 operation sequence.  Every wait is
 // bounded: on time-out the kernel records KTUNE_ETIMEOUT, drains its own
@@ -43,34 +43,6 @@ constexpr int kEpiWarps = 16;                             // 4 per tensor-memory
 constexpr int kPipeThreads = 64 + 32 * kEpiWarps;
 constexpr unsigned FULL = 0xffffffffu;
 
-// GELU(z) = z (1 + erf(z / sqrt 2)) / 2 with erf from Abramowitz & Stegun,
-// Handbook of Mathematical Functions, formula 7.1.28 (Hastings):
-//   erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16 + e(x),  x >= 0,
-//   |e(x)| <= 3e-7.
-// The bracket's inverse 16th power is erfc(|x|), so 1 + erf(z / sqrt 2) is
-// 2 - erfc for z >= 0 and erfc itself for z < 0 (no cancellation for negative
-// z).  For z >= 16 the power overflows, erfc is 0 and GELU(z) = z exactly.
-// With float32 arithmetic the result is within 4e-7 max(|z|, 1) of the exact
-// GELU (a float64 comparison over a dense grid of [-12, 20]), far below the
-// bfloat16 rounding the activation then takes.
-__device__ __forceinline__ float gelu_p(float z) {
-  const float x = fabsf(z) * 0.70710678118654752f;
-  float p = fmaf(4.30638e-5f, x, 2.765672e-4f);
-  p = fmaf(p, x, 1.520143e-4f);
-  p = fmaf(p, x, 9.2705272e-3f);
-  p = fmaf(p, x, 4.22820123e-2f);
-  p = fmaf(p, x, 7.05230784e-2f);
-  p = fmaf(p, x, 1.0f);
-  p = p * p;
-  p = p * p;
-  p = p * p;
-  p = p * p;
-  float q;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(p));
-  const float t = z >= 0.0f ? 2.0f - q : q;
-  return 0.5f * z * t;
-}
-
 __device__ __forceinline__ int okey_p(float f) {
   const int b = __float_as_int(f);
   return b >= 0 ? b : b ^ 0x7FFFFFFF;
@@ -82,6 +54,66 @@ __device__ __forceinline__ uint32_t bf2(float lo, float hi) {
   const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t *>(&b);
 }
+
+// GELU(z) = z (1 + erf(z / sqrt 2)) / 2 with erf from Abramowitz & Stegun,
+// Handbook of Mathematical Functions, formula 7.1.28 (Hastings):
+//   erf(x) = 1 - (1 + a1 x + a2 x^2 + ... + a6 x^6)^-16 + e(x),  x >= 0,
+//   |e(x)| <= 3e-7.
+// The bracket's inverse 16th power is erfc(|x|), so 1 + erf(z / sqrt 2) is
+// 2 - erfc for z >= 0 and erfc itself for z < 0 (no cancellation for negative
+// z).  For z >= 16 the power overflows, erfc is 0 and GELU(z) = z exactly.
+// With float32 arithmetic the result is within 4e-7 max(|z|, 1) of the exact
+// GELU (a float64 comparison over a dense grid of [-12, 20]), far below the
+// bfloat16 rounding the activation then takes.
+// Two GELUs at once, of z = v + bias for both halves, with the paired f32x2
+// instructions of sm_100 and later (each half one IEEE round-to-nearest
+// operation, in the order of the formula above); returns their
+// round-to-nearest-even bfloat16 pair.
+__device__ __forceinline__ uint64_t f2pk(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t gelu2_bf(float v0, float b0, float v1, float b1) {
+  const uint64_t z = f2add(f2pk(v0, v1), f2pk(b0, b1));
+  const uint64_t x = f2mul(z & 0x7FFFFFFF7FFFFFFFull, f2pk(0.70710678118654752f, 0.70710678118654752f));
+  uint64_t p = f2fma(f2pk(4.30638e-5f, 4.30638e-5f), x, f2pk(2.765672e-4f, 2.765672e-4f));
+  p = f2fma(p, x, f2pk(1.520143e-4f, 1.520143e-4f));
+  p = f2fma(p, x, f2pk(9.2705272e-3f, 9.2705272e-3f));
+  p = f2fma(p, x, f2pk(4.22820123e-2f, 4.22820123e-2f));
+  p = f2fma(p, x, f2pk(7.05230784e-2f, 7.05230784e-2f));
+  p = f2fma(p, x, f2pk(1.0f, 1.0f));
+  p = f2mul(p, p);
+  p = f2mul(p, p);
+  p = f2mul(p, p);
+  p = f2mul(p, p);
+  float p0, p1, z0, z1, q0, q1;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(p0), "=f"(p1) : "l"(p));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(z0), "=f"(z1) : "l"(z));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q0) : "f"(p0));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q1) : "f"(p1));
+  const float t0 = z0 >= 0.0f ? 2.0f - q0 : q0, t1 = z1 >= 0.0f ? 2.0f - q1 : q1;
+  const uint64_t g = f2mul(f2mul(f2pk(0.5f, 0.5f), z), f2pk(t0, t1));
+  float g0, g1;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(g0), "=f"(g1) : "l"(g));
+  return bf2(g0, g1);
+}
+
 
 // 32 lanes x 32 columns of FP32 accumulators in one load.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -314,10 +346,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
               const float4 b0 = *reinterpret_cast<const float4 *>(bias + c0 + e8);
               const float4 b1 = *reinterpret_cast<const float4 *>(bias + c0 + e8 + 4);
               uint4 q;
-              q.x = bf2(gelu_p(__fadd_rn(v[e8 + 0], b0.x)), gelu_p(__fadd_rn(v[e8 + 1], b0.y)));
-              q.y = bf2(gelu_p(__fadd_rn(v[e8 + 2], b0.z)), gelu_p(__fadd_rn(v[e8 + 3], b0.w)));
-              q.z = bf2(gelu_p(__fadd_rn(v[e8 + 4], b1.x)), gelu_p(__fadd_rn(v[e8 + 5], b1.y)));
-              q.w = bf2(gelu_p(__fadd_rn(v[e8 + 6], b1.z)), gelu_p(__fadd_rn(v[e8 + 7], b1.w)));
+              q.x = gelu2_bf(v[e8 + 0], b0.x, v[e8 + 1], b0.y);
+              q.y = gelu2_bf(v[e8 + 2], b0.z, v[e8 + 3], b0.w);
+              q.z = gelu2_bf(v[e8 + 4], b1.x, v[e8 + 5], b1.y);
+              q.w = gelu2_bf(v[e8 + 6], b1.z, v[e8 + 7], b1.w);
               *reinterpret_cast<uint4 *>(H + tc::core_off(row, c0 + e8, kMlpHidden)) = q;
             }
           }
