@@ -308,8 +308,9 @@ int ktune_search_set_neighbourhood(ktune_search *search, int radius);
  * digits by ordinal into a scratch list of N words (so it also writes score 0
  * for the configurations evaluated before the step, which the four kernels
  * leave untouched there), and only shape 2 is offered (others: KTUNE_ESTATE).
- * Shape 2 is the default for the searches it applies to; other searches
- * refuse shapes > 0 (KTUNE_ESTATE).
+ * Shape 2 is the default for the searches it applies to whose TS holds at
+ * least 2^18 configurations (smaller ones default to shape 0, whose fixed cost
+ * is lower); other searches refuse shapes > 0 (KTUNE_ESTATE).
  * Cached predictions and neighbourhood-restricted steps keep their own
  * kernels.  Synchronises the search's last stream. */
 int ktune_search_set_fused(ktune_search *search, int shape);

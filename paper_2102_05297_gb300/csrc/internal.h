@@ -61,6 +61,7 @@ __host__ __device__ inline int pack_tree_bytes(int D, bool narrow) {
 
 // ---- batched step (k_batch.cu): one launch of each kernel serves S searches ----
 constexpr int kSubTile = 1024;          // configurations per weight sub-tile
+constexpr int64_t kFusedDefaultMin = 1 << 18;   // smallest TS stepped by one persistent kernel by default
 constexpr int kSuper = 32;              // sub-tiles per super-tile (select hierarchy)
 constexpr int kMaxSuper = 4096;         // => at most 134M valid configurations per search
 constexpr int kOtfRun = 4;              // raw indices per thread per decode round (on-the-fly)
