@@ -219,6 +219,22 @@ def test_every_score_on_the_fly(kt, name, select, k, fused):
         zero_evaluated=bool(fused), fused=fused)
 
 
+@pytest.mark.parametrize("fused", [2, 0])
+def test_every_score_on_the_fly_window_tables(kt, fused):
+    """An on-the-fly space whose constrained parameters have too many value
+    combinations for one table bit each (validity by window tables and the
+    general check) and whose fastest radices are not powers of two (an
+    odometer step per raw index): 1.87M raw configurations."""
+    values = [list(range(1, r + 1)) for r in (3, 5, 7, 9, 10, 11, 6, 3)]
+    code = W.c_sum_le([0, 1, 2, 3], 16) + W.c_sum_le([4, 5, 6, 7], 22) + W.c_product_le([1, 5], 40)
+    d = W.SpaceDesc("windows_8p", ["p%d" % j for j in range(8)], values, code)
+    assert d.n_raw == 1871100
+    roles = W.layout(16)
+    model = random_model(d.radices, roles, depth=10, seed=61)
+    run(kt, d, model, steps=3, k=6, seed=3, flags=kt.KTUNE_ON_THE_FLY, fseed=4,
+        zero_evaluated=bool(fused), fused=fused)
+
+
 def test_readback_rules(kt):
     import torch
     d = W.load_space("batch_2")
