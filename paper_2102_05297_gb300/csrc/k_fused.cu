@@ -1,20 +1,25 @@
-// One whole search step of a tree-model search over a materialised space in
-// the one-word digit layout, as a single persistent kernel (a cooperative
-// launch: one CTA per SM, all resident at once).
+// One whole search step of a tree-model search over a space in the one-word
+// digit layout (materialised, or decoded on the fly), as a single persistent
+// kernel (a cooperative launch: one CTA per SM, all resident at once).
 //
-//   P0  every CTA: the leaf c_profile reaches in each tree (a6, Section
-//       3.3.2; warp 0, one lane per tree) and the active counters (Delta and
-//       the prediction of c_profile both non-zero, PC_used of Eq. score).
+//   P0  every CTA: the leaf c_profile reaches in the trees of the counters
+//       whose Delta is not 0 (a6, Section 3.3.2; warp 0, one lane per tree),
+//       and the active counters (Delta and the prediction of c_profile both
+//       non-zero, PC_used of Eq. score).
+//   PD  on the fly only: the grid's warps decode the raw tiles holding a valid
+//       configuration and write TS's one-word digits by ordinal (a1, a2).
+//   P0b every CTA, its share of the per-leaf summands of Eq. score of all
+//       active trees (a8).
+//   --  grid barrier A (every wait bounded).
 //   P1  every CTA, a contiguous range of TS: for each group of active trees
-//       that fits shared memory, the node words are copied in and the
-//       per-leaf summands of Eq. score are computed from the leaf values;
-//       then every configuration walks the group's trees and adds the
+//       that fits shared memory, their node words and summands are copied
+//       in; every configuration walks the group's trees and adds the
 //       summands of the leaves it reaches (a3, a7, a8).  CTA minimum and
-//       maximum over the unevaluated ones by ordered-int atomics (a9).
-//   --  grid barrier (every wait bounded): s_min, s_max are final.
-//   P2  every warp, one 1024-configuration sub-tile at a time: Eq.
-//       score_normalization and the integer weights, the sub-tile sum and the
-//       super-tile sums (a10).
+//       maximum over the unevaluated ones by ordered-int atomics (a9), or the
+//       CTA's top-k list.
+//   --  grid barrier B (weighted draws only): s_min, s_max are final.
+//   P2  every warp, 512 configurations at a time: Eq. score_normalization and
+//       the integer weights, added to the sub-tile and super-tile sums (a10).
 //   P3  the CTA that finishes last: the k weighted draws without replacement
 //       of Algorithm 1 over the super-tile / sub-tile / configuration
 //       hierarchy (a11), or the merge of the CTAs' top-k lists; the picks are
@@ -536,10 +541,10 @@ __device__ __forceinline__ uint64_t packed_of_word(const SearchDev &sd, uint32_t
 // raw tiles (4096 raw indices each) that hold a valid configuration in turn
 // (the list is made when the space is created; the tiles without one are
 // never visited) and decode them (a lane takes four consecutive indices of
-// each round of 128), check the
-// constraints, and write the one-word digits of every valid configuration
-// at its ordinal in fa.list (the tile's valid prefix plus its rank, counted
-// with warp scans).  TS is thus rebuilt in every step, never kept.
+// each round of 128), check the constraints, and write the one-word digits
+// of every valid configuration at its ordinal in fa.list (the tile's valid
+// prefix plus its rank, counted with warp scans).  TS is thus rebuilt in
+// every step, never kept.
 __device__ __noinline__ void fused_decode(const FusedArgs &fa) {
   const SearchDev &sd = fa.sd;
   OtfCtx *ctx = reinterpret_cast<OtfCtx *>(fz_smem);
