@@ -299,6 +299,8 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
   __shared__ int sh_n;
   __shared__ uint32_t pick_w[KTUNE_MAX_K];   // the picks' weights
   __shared__ int64_t spec_g[kSpec];          // the sub-tile fetched into buffer b (-1: none)
+  __shared__ uint64_t spec_base[kSpec];      // the weight before that sub-tile, and its sum,
+  __shared__ uint64_t spec_vg[kSpec];        // both before this step's draws
   const int64_t n_sub = (N + kSubTile - 1) / kSubTile;
   const int64_t n_super = (n_sub + kSuper - 1) / kSuper;
   uint64_t *sup = reinterpret_cast<uint64_t *>(smem);   // super-tile sums
@@ -439,7 +441,11 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
       uint64_t vg, r2;
       if (locate(r, local, incl, sp, g, gl, vg, r2)) {
         fetch(warp, g);
-        if (lane == 0) spec_g[warp] = g;
+        if (lane == 0) {
+          spec_g[warp] = g;
+          spec_base[warp] = r - r2;
+          spec_vg[warp] = vg;
+        }
       }
     }
   }
@@ -458,13 +464,35 @@ __device__ __noinline__ int fused_draws(const FusedArgs &fa, int64_t *pick) {
       if (W == 0) break;
       const uint64_t uj = j < 32 ? __shfl_sync(kFullMask, u_lo, j) : __shfl_sync(kFullMask, u_hi, j - 32);
       const uint64_t r = scaled_draw(uj, W);
-      int64_t sp, g;
-      int gl;
-      uint64_t vg, r2;
-      if (!locate(r, local, incl, sp, g, gl, vg, r2)) break;   // cannot happen with consistent sums
-      const unsigned has = __ballot_sync(kFullMask, (int64_t)my_spec == g);
-      const int bsel = has ? __ffs(has) - 1 : kSpec;
-      if (bsel == kSpec) fetch(kSpec, g);
+      int64_t sp = 0, g = -1;
+      int gl = 0, bsel = kSpec;
+      uint64_t vg = 0, r2 = 0;
+      // the sub-tile fetched for this draw, as the earlier picks left it: the
+      // weight before it and its sum, less the picks before and inside it
+      if (j < kSpec && spec_g[j] >= 0) {
+        const int64_t gs = spec_g[j];
+        uint64_t before = 0, inside = 0;
+        for (int q = 0; q < count; ++q) {
+          const int64_t pq = pick[q];
+          if (pq < gs * kSubTile) before += pick_w[q];
+          else if (pq < (gs + 1) * kSubTile) inside += pick_w[q];
+        }
+        const uint64_t base = spec_base[j] - before, vr = spec_vg[j] - inside;
+        if (r >= base && r - base < vr) {   // the draw lands there
+          g = gs;
+          sp = gs / kSuper;
+          gl = (int)(gs - sp * kSuper);
+          vg = vr;
+          r2 = r - base;
+          bsel = j;
+        }
+      }
+      if (g < 0) {   // elsewhere: the three-level search
+        if (!locate(r, local, incl, sp, g, gl, vg, r2)) break;   // cannot happen with consistent sums
+        const unsigned has = __ballot_sync(kFullMask, (int64_t)my_spec == g);
+        bsel = has ? __ffs(has) - 1 : kSpec;
+        if (bsel == kSpec) fetch(kSpec, g);
+      }
       // the group: the group prefix sums less the earlier picks' weights in
       // this sub-tile up to the group (lane q < count holds pick q)
       const bool here = lane < count && (int64_t)(my_pick / kSubTile) == g;
