@@ -416,6 +416,12 @@ def headline_roofline(fused, kern_ms, achieved, peak_visits, props, sm_mhz, src)
         names = ("predict_cprofile", "summands_barrier", "walk", "barrier_wait", "weights",
                  "last_cta_slack", "draws")
         r["phase_share"] = {n: kern_ms[1 + i] / tot for i, n in enumerate(names)}
+        # the walk phase alone (its share of the kernel's duration, from the
+        # phase stamps): the part of the step the derived peak describes
+        walk = r["phase_share"]["walk"]
+        if walk > 0:
+            r["walk_phase"] = {"achieved": achieved / walk / 1e9, "frac": achieved / walk / peak_visits,
+                               "unit": "Gvisit/s"}
     else:
         tot = kern_ms[:4].sum()
         r["kernel"] = "k_bscore (tree walk + Eq. score)"
@@ -972,7 +978,9 @@ def path_large(ctx, depth=12):
                      "achieved": ach / 1e9, "peak": peak / 1e9, "unit": "Gvisit/s",
                      "frac": ach / peak, "traffic": PROFILED_TRAFFIC.get("k_step_fused_otf"),
                      "mean_active_counters": float(np.mean(nact)),
-                     "phase_share": {n: kern_ms[1 + i] / kern_ms[0] for i, n in enumerate(names) if n}},
+                     "phase_share": {n: kern_ms[1 + i] / kern_ms[0] for i, n in enumerate(names) if n},
+                     "walk_phase": {"achieved": visits / (kern_ms[3] / 1e3) / 1e9,
+                                    "frac": visits / (kern_ms[3] / 1e3) / peak, "unit": "Gvisit/s"}},
     }
 
 
