@@ -833,12 +833,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
   const bool cta0 = blockIdx.x == 0;
   stamp(fa, 0, cta0);
   const int64_t lo = N * (int64_t)blockIdx.x / G, hi = N * (int64_t)(blockIdx.x + 1) / G;
-  // this CTA's digits and evaluated bits, brought into L2 while c_profile's walk runs
-  if (!OTF)
-    for (int64_t off = (int64_t)threadIdx.x * 32; off < hi - lo; off += (int64_t)THREADS * 32)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.narrow + lo + off));
-  for (int64_t off = (int64_t)threadIdx.x * 32; off < (hi - lo) / 32 + 1; off += (int64_t)THREADS * 32)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.eval + (lo >> 5) + off));
   // ---- P0: c_profile's prediction per counter, the active counters ----------------
   // Only the counters with Delta_p != 0 (known before the step) can be
   // active, so only their trees are walked for c_profile: their node bytes
@@ -867,6 +861,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_fused(const __grid_constant
     const int per16 = L >> 4, n16 = n_cand * per16;
     for (int i = threadIdx.x; i < n16; i += THREADS)
       cp_async16(smem + 16 * (size_t)i, sd.nodes + (size_t)sh_active[i / per16] * L + 16 * (size_t)(i % per16));
+  }
+  // this CTA's digits and evaluated bits, brought into L2 while c_profile's
+  // walk runs (requested after the trees' node bytes, which the walk waits for)
+  if (!OTF)
+    for (int64_t off = (int64_t)threadIdx.x * 32; off < hi - lo; off += (int64_t)THREADS * 32)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.narrow + lo + off));
+  for (int64_t off = (int64_t)threadIdx.x * 32; off < (hi - lo) / 32 + 1; off += (int64_t)THREADS * 32)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(sd.eval + (lo >> 5) + off));
+  if (staged) {
     cp_async_wait_all();
     __syncthreads();
   }
