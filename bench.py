@@ -76,8 +76,8 @@ PROFILED_TRAFFIC = {
     "k_cscore_leaf": 36.564e6,    # profiles/cached_mid_12p.md
     "k_mlp_pipe": 18.748e6,       # profiles/k_mlp_pipe_mid_12p.md
     "k_bscore_otf": 20.228e6,     # profiles/k_bscore_otf_large_16p.md
-    "k_step_fused": 9.762e6,      # profiles/k_step_fused_mid_12p.md
-    "k_step_fused_otf": 378.5e6,  # profiles/k_step_fused_otf_large_16p.md
+    "k_step_fused": 9.763e6,      # profiles/k_step_fused_mid_12p.md
+    "k_step_fused_otf": 378.7e6,  # profiles/k_step_fused_otf_large_16p.md
 }
 MLP_HIDDEN = 256
 
