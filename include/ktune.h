@@ -219,7 +219,9 @@ int ktune_search_set_profile(ktune_search *search, int64_t raw);
  * their raw indices (out_raw, HOST int64[k]) and raw scores (out_score, HOST
  * float[k]) in selection order; *n_out = number written.  If fewer than k
  * configurations remain unevaluated, all of them are returned and the call
- * returns KTUNE_EXHAUSTED. */
+ * returns KTUNE_EXHAUSTED.  The step's kernels write the selections into
+ * mapped pinned host memory that the search owns; the call synchronises the
+ * search's stream and copies them out (no device-to-host copy is enqueued). */
 int ktune_step(ktune_search *search, const float *profiled_counters, int k,
                int64_t *out_raw, float *out_score, int *n_out);
 /* The same step with DEVICE output buffers, enqueued on `stream` without
