@@ -33,8 +33,12 @@ def drive(s, gpu, radices, steps, k=None):
     return out
 
 
-@pytest.mark.parametrize("name,K,depth", [("batch_4", 32, 12), ("batch_3", 40, 10), ("batch_2", 16, 6)])
-def test_cached_tree_steps_equal_fused(kt, name, K, depth):
+@pytest.mark.parametrize("name,K,depth,shape", [("batch_4", 32, 12, None), ("batch_3", 40, 10, None),
+                                                ("batch_2", 16, 6, None), ("batch_4", 32, 12, 2),
+                                                ("batch_3", 40, 10, 2)])
+def test_cached_tree_steps_equal_fused(kt, name, K, depth, shape):
+    """Cached steps against steps that predict again; shape 2: the steps
+    that predict again run as one persistent kernel."""
     d = W.load_space(name)
     roles = W.layout(K)
     model = random_model(d.radices, roles, depth=depth, seed=K + depth)
@@ -43,6 +47,9 @@ def test_cached_tree_steps_equal_fused(kt, name, K, depth):
     m = kt.Model(sp, model)
     a = kt.Search(sp, m, k=6, seed=9)
     b = kt.Search(sp, m, k=6, seed=9)
+    if shape is not None:
+        a.set_fused(shape)
+        b.set_fused(shape)
     b.set_cached(True)
     assert drive(a, gpu, d.radices, 8) == drive(b, gpu, d.radices, 8)
     st_a, st_b = a.stats(), b.stats()
