@@ -1232,6 +1232,17 @@ def cpu_baseline(name, model, counters, n_sample=None):
     return out
 
 
+def oracle_count(wl):
+    """The space's valid count as the oracle wrote it (tests/golden/space_counts.json,
+    written by tests/golden/make_spaces.py with oracle.space.count_valid), so
+    that the reference line names the same configuration as the library's."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "space_counts.json")) as f:
+            return int(json.load(f)[wl["space"]]["n_valid"])
+    except (OSError, KeyError, TypeError, ValueError):
+        return -1
+
+
 def run_reference(args):
     """The oracle as the reference arm: --steps timed oracle steps, each over
     a bounded uniform sample of the workload (no GPU used)."""
@@ -1268,7 +1279,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "configs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": describe(name, wl, desc, -1), "cpu_baseline": cb,
+        "data": "synthetic", "config": describe(name, wl, desc, oracle_count(wl)), "cpu_baseline": cb,
         "e2e": {"value": v, "unit": "configs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
