@@ -464,6 +464,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int64_t t = it.lo + warp; t < it.hi; t += kBWarps) {
           const uint32_t tbase = (uint32_t)(t * kEnumTileRaw);
           int64_t ord_base = __ldg(sd.tile_offset + t);
+          if (__ldg(sd.tile_offset + t + 1) == ord_base) continue;   // no valid configuration here
           uint32_t W = otf_decode(ctx, tbase + 4u * (uint32_t)lane);
           uint32_t xci = use_ci ? otf_ci(ctx, W) : 0u;
           for (int q = 0; q < kEnumTileRaw / 128; ++q) {
